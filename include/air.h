@@ -1,0 +1,176 @@
+/* air.h -- C ABI of the GB300 adaptive image ray-tracing (AIR) library.
+ *
+ * Method: E. R. Parkin (2010), "Adaptive image ray-tracing for astrophysical
+ * simulations" (MNRAS Letters; arXiv:1010.5534).
+ *
+ * Conventions for every entry point
+ *   - Plain C types only; no exceptions cross the ABI. Every call returns an
+ *     air_status; on failure air_last_error() gives a message (thread-local,
+ *     valid until the next call on the same thread).
+ *   - Device work is ordered on the handle's CUDA stream (air_set_stream).
+ *     Calls that return results to the caller synchronise that stream before
+ *     returning; inputs are copied, the caller keeps ownership of its arrays.
+ *   - Buffers of an air_image are host or device memory, as its `mem` field
+ *     says; they are caller-owned and caller-sized (`capacity` entries).
+ *   - Images are orthographic (the paper's observer is at 1 kpc from a box of
+ *     1e18 cm, Section 3). Pixel (L, i, j) of an n0 x n0 base image has its
+ *     centre at u = -H + (i + 1/2) 2H / (n0 2^L), v likewise with j, where the
+ *     image basis is u = normalize(up x dir), v = dir x u and H = half_extent.
+ *   - Cells are half-open [x_k, x_k+1): a ray lying exactly on a cell face
+ *     samples the cell of higher index.
+ */
+#ifndef AIR_H
+#define AIR_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define AIR_API __attribute__((visibility("default")))
+#else
+#define AIR_API
+#endif
+
+typedef enum {
+  AIR_OK = 0,
+  AIR_ERR_ARG = 1,      /* invalid argument or input field value */
+  AIR_ERR_OOM = 2,      /* device or host allocation failed */
+  AIR_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+  AIR_ERR_CAPACITY = 4, /* output arrays too small: n_out holds the size needed */
+  AIR_ERR_TIMEOUT = 5,  /* a bounded device wait gave up */
+  AIR_ERR_NUMERIC = 6   /* non-finite result */
+} air_status;
+
+typedef enum { AIR_GRID_UNIFORM = 0, AIR_GRID_AMR = 1 } air_grid_kind;
+typedef enum { AIR_F32 = 0, AIR_F64 = 1 } air_dtype;
+typedef enum { AIR_HOST = 0, AIR_DEVICE = 1 } air_mem;
+
+/* Simulation grid (Section 2 step i; Section 3: FLASH/PARAMESH block AMR).
+ * Uniform: n[0] x n[1] x n[2] cells over the box [lo, hi]; fields laid out
+ *   [n2][n1][n0], x fastest.
+ * Block AMR: n[] base cells per axis, cut into cubic bricks of `brick` cells
+ *   (a power of two dividing every n[a]); `max_level` refinement levels by a
+ *   factor 2. Only LEAF bricks are given: brick b sits at level brick_level[b]
+ *   with its lowest corner at brick_origin[3b..3b+2] in units of the finest
+ *   cell (n[a] << max_level per axis); the leaf bricks must tile the box
+ *   exactly. Fields are [n_bricks][brick][brick][brick], x fastest.
+ * Emission (Section 1: column density and emergent intensity): per band b,
+ *   emissivity j_b = rho^2 Lambda_b(T) (emis_mode 1) or rho^2 (emis_mode 0),
+ *   absorption coefficient alpha_b = kappa[b] rho. Lambda_b is tabulated at
+ *   n_tbins points uniform in log10 T over [logT_lo, logT_hi] and interpolated
+ *   linearly in log10 T, clamped at both ends.
+ * Fields must be finite, rho >= 0 and T > 0 (checked on the device). */
+typedef struct {
+  int32_t kind;          /* air_grid_kind */
+  int32_t n[3];
+  double lo[3], hi[3];
+  int32_t brick, max_level, n_bricks;
+  const int32_t *brick_level;   /* [n_bricks], host memory */
+  const int32_t *brick_origin;  /* [n_bricks][3], host memory */
+  int32_t field_dtype;          /* air_dtype of rho and temp */
+  const void *rho;              /* host memory */
+  const void *temp;             /* host memory; may be NULL when emis_mode == 0 */
+  int32_t n_bands, emis_mode;
+  const float *lambda_table;    /* [n_bands][n_tbins], host memory */
+  int32_t n_tbins;
+  double logT_lo, logT_hi;
+  const double *kappa;          /* [n_bands], host memory */
+} air_grid_desc;
+
+typedef struct {
+  double dir[3];      /* direction the rays travel (need not be normalised) */
+  double up[3];       /* must not be parallel to dir */
+  double center[3];   /* world point at the image centre */
+  double half_extent; /* H > 0 */
+} air_view;
+
+/* Adaptive image parameters (Section 2 steps iii-v; Section 3 Eq. 1, Eq. 2). */
+typedef struct {
+  int32_t base_res;   /* n0: base image n0 x n0 (step i) */
+  int32_t max_level;  /* maximum image refinement level, n0 << max_level <= 2^20 */
+  double xi_crit;     /* refine a pixel when xi >= xi_crit (>= 0) */
+  int32_t xi_norm;    /* Eq. 2 denominator: 0 = sum over the axis u only (reduces to
+                         Eq. 1 in 1-D, bounded by 1), 1 = literal sum over u and v */
+  int32_t refine_on;  /* parameter p: 0 = band-summed intensity, 1 = column density,
+                         2 = refine when either parameter is flagged */
+  int32_t fp64_level; /* AMR bricks at this level or deeper get FP64 entry/exit
+                         parameters; negative = library default (3) */
+  int32_t include_interior; /* 0: output the leaf pixels (the final image);
+                               1: output every traced pixel, interior ones too */
+} air_params;
+
+/* Output image: one entry per pixel. Leaves (or all traced nodes) come in
+ * creation order: the base image row-major, then, sweep by sweep, the four
+ * children of each refined pixel (child c at (2i + (c & 1), 2j + (c >> 1))) in
+ * the order of their parents. Optional arrays may be NULL. */
+typedef struct {
+  int32_t mem;         /* air_mem of every array below */
+  int64_t capacity;    /* entries available in each per-pixel array */
+  int64_t n_out;       /* out: entries written (or needed, on AIR_ERR_CAPACITY) */
+  int64_t n_leaves;    /* out: leaf pixels of the final image */
+  int64_t n_rays;      /* out: traced rays = all tree nodes (Table 1 "Pixels") */
+  int64_t n_steps;     /* out: ray-cell segments marched, summed over all rays */
+  int32_t n_sweeps;    /* out: refinement sweeps that refined something */
+  int32_t *level;      /* [capacity] optional */
+  int32_t *i, *j;      /* [capacity] optional */
+  uint8_t *is_leaf;    /* [capacity] optional */
+  float *coldens;      /* [capacity] column density, optional */
+  float *intensity;    /* [n_bands][capacity] band-major, optional */
+  float *p;            /* [capacity] band-summed intensity as used by the scan, optional */
+  double *band_flux;   /* [n_bands] sum over leaves of I_b x pixel area, optional */
+} air_image;
+
+typedef struct air_grid air_grid;
+
+/* Copy a grid to the device and build its brick lookup (Section 2 step i).
+ * `stream` is a cudaStream_t (NULL = legacy default stream). On success *out
+ * owns the device copy until air_free. */
+AIR_API air_status air_load_grid(const air_grid_desc *desc, void *stream, air_grid **out);
+
+/* Change the stream later calls on this handle are ordered on. */
+AIR_API air_status air_set_stream(air_grid *g, void *stream);
+
+/* Fixed-resolution image (the paper's comparison arm, Section 3 / Table 1):
+ * one ray per pixel of a res x res image, output row-major (pixel (i, j) at
+ * entry j * res + i, level 0). `fp64_level` as in air_params. */
+AIR_API air_status air_render_fixed(air_grid *g, const air_view *view, int32_t res, int32_t fp64_level,
+                            air_image *out);
+
+/* Adaptive image (Section 2 steps i-vi): trace the base image, then repeat
+ * {scan every leaf below max_level with Eq. 2, flag xi >= xi_crit, extend the
+ * flags so adjacent pixels differ by at most one level, split every flagged
+ * pixel into four and trace the new rays} until no pixel is flagged. */
+AIR_API air_status air_render_adaptive(air_grid *g, const air_view *view, const air_params *params,
+                               air_image *out);
+
+/* Phase profiling: when enabled, every kernel launch group of a render is
+ * bracketed by CUDA events on the handle's stream, and the elapsed device time
+ * is added per phase when the render completes. Enabling resets the counters. */
+enum {
+  AIR_PHASE_MARCH = 0,   /* ray march (Section 2 step ii) */
+  AIR_PHASE_SCAN = 1,    /* truncation-error scan, Eq. 2 (step iii) */
+  AIR_PHASE_BALANCE = 2, /* 2:1 level balance (step iii) */
+  AIR_PHASE_REFINE = 3,  /* prefix sum + child emission (step iv) */
+  AIR_PHASE_OUTPUT = 4,  /* leaf compaction + band flux (step vi) */
+  AIR_N_PHASES = 5
+};
+AIR_API air_status air_profile_enable(air_grid *g, int32_t on);
+/* ms[p]: summed device milliseconds, launches[p]: kernel launches, for each
+ * phase p < AIR_N_PHASES (either pointer may be NULL). */
+AIR_API air_status air_profile_read(air_grid *g, double *ms, int64_t *launches);
+
+/* Release the device copy and every buffer the handle holds. NULL is a no-op. */
+AIR_API void air_free(air_grid *g);
+
+/* Message for the last failing call on this thread ("" if none). */
+AIR_API const char *air_last_error(void);
+
+/* Library version string. */
+AIR_API const char *air_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

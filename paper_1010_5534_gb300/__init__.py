@@ -1,0 +1,299 @@
+"""Python binding of the GB300 adaptive image ray-tracing (AIR) library.
+
+Thin ctypes layer over the C ABI in include/air.h: it marshals arguments,
+allocates outputs (torch device tensors, or pinned host tensors) and passes
+torch's current CUDA stream. Every step of the method runs in the library's
+CUDA kernels; there is no fallback. If the shared library is missing, calls
+raise RuntimeError.
+
+Method: E. R. Parkin (2010), "Adaptive image ray-tracing for astrophysical
+simulations", Section 2 (the AIR steps) and Section 3 (Eq. 1, Eq. 2).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_CSRC = os.path.join(_HERE, "csrc")
+_BUILD = os.path.join(_HERE, "_build")
+LIB_PATH = os.path.join(_HERE, "libair_gb300.so")
+SOURCES = ["air_api.cu", "air_grid.cu", "air_march.cu", "air_refine.cu"]
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
+              "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
+
+AIR_OK, AIR_ERR_ARG, AIR_ERR_OOM, AIR_ERR_CUDA, AIR_ERR_CAPACITY, AIR_ERR_TIMEOUT, \
+    AIR_ERR_NUMERIC = range(7)
+AIR_HOST, AIR_DEVICE = 0, 1
+
+EXPORTED = ["air_load_grid", "air_set_stream", "air_render_fixed", "air_render_adaptive",
+            "air_profile_enable", "air_profile_read", "air_free", "air_last_error", "air_version"]
+PHASES = ("march", "scan", "balance", "refine", "output")
+
+
+def _nvcc():
+    for c in ("/usr/local/cuda/bin/nvcc", "nvcc"):
+        if os.path.sep not in c or os.path.exists(c):
+            return c
+    return "nvcc"
+
+
+def build(verbose: bool = False, force: bool = False) -> str:
+    """Compile csrc/*.cu for sm_103a (one nvcc per translation unit, in
+    parallel) and link paper_1010_5534_gb300/libair_gb300.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = [os.path.join(_CSRC, s) for s in SOURCES]
+    deps = srcs + [os.path.join(_CSRC, f) for f in os.listdir(_CSRC) if f.endswith(".cuh")] + \
+        [os.path.join(_HERE, "..", "include", "air.h")]
+    newest = max(os.path.getmtime(p) for p in deps)
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    nvcc = _nvcc()
+    procs, objs = [], []
+    for s in srcs:
+        o = os.path.join(_BUILD, os.path.basename(s) + ".o")
+        objs.append(o)
+        cmd = [nvcc, *NVCC_FLAGS, "-c", s, "-o", o]
+        if verbose:
+            print(" ".join(cmd))
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    for cmd, p in procs:
+        out, _ = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError(f"nvcc failed: {' '.join(cmd)}\n{out.decode(errors='replace')}")
+        if verbose and out:
+            print(out.decode(errors="replace"))
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    cmd = [nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp, *objs]
+    r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout.decode(errors='replace')}")
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+# ---------------------------------------------------------------- structures
+class GridDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n", C.c_int32 * 3), ("lo", C.c_double * 3),
+                ("hi", C.c_double * 3), ("brick", C.c_int32), ("max_level", C.c_int32),
+                ("n_bricks", C.c_int32), ("brick_level", C.c_void_p),
+                ("brick_origin", C.c_void_p), ("field_dtype", C.c_int32), ("rho", C.c_void_p),
+                ("temp", C.c_void_p), ("n_bands", C.c_int32), ("emis_mode", C.c_int32),
+                ("lambda_table", C.c_void_p), ("n_tbins", C.c_int32), ("logT_lo", C.c_double),
+                ("logT_hi", C.c_double), ("kappa", C.c_void_p)]
+
+
+class View(C.Structure):
+    _fields_ = [("dir", C.c_double * 3), ("up", C.c_double * 3), ("center", C.c_double * 3),
+                ("half_extent", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [("base_res", C.c_int32), ("max_level", C.c_int32), ("xi_crit", C.c_double),
+                ("xi_norm", C.c_int32), ("refine_on", C.c_int32), ("fp64_level", C.c_int32),
+                ("include_interior", C.c_int32)]
+
+
+class Image(C.Structure):
+    _fields_ = [("mem", C.c_int32), ("capacity", C.c_int64), ("n_out", C.c_int64),
+                ("n_leaves", C.c_int64), ("n_rays", C.c_int64), ("n_steps", C.c_int64),
+                ("n_sweeps", C.c_int32), ("level", C.c_void_p), ("i", C.c_void_p),
+                ("j", C.c_void_p), ("is_leaf", C.c_void_p), ("coldens", C.c_void_p),
+                ("intensity", C.c_void_p), ("p", C.c_void_p), ("band_flux", C.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded C library. Raises RuntimeError if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "paper_1010_5534_gb300.build() (nvcc, sm_103a)")
+            L = C.CDLL(LIB_PATH)
+            L.air_load_grid.restype = C.c_int
+            L.air_load_grid.argtypes = [C.POINTER(GridDesc), C.c_void_p, C.POINTER(C.c_void_p)]
+            L.air_set_stream.restype = C.c_int
+            L.air_set_stream.argtypes = [C.c_void_p, C.c_void_p]
+            L.air_render_fixed.restype = C.c_int
+            L.air_render_fixed.argtypes = [C.c_void_p, C.POINTER(View), C.c_int32, C.c_int32,
+                                           C.POINTER(Image)]
+            L.air_render_adaptive.restype = C.c_int
+            L.air_render_adaptive.argtypes = [C.c_void_p, C.POINTER(View), C.POINTER(Params),
+                                              C.POINTER(Image)]
+            L.air_profile_enable.restype = C.c_int
+            L.air_profile_enable.argtypes = [C.c_void_p, C.c_int32]
+            L.air_profile_read.restype = C.c_int
+            L.air_profile_read.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+            L.air_free.restype = None
+            L.air_free.argtypes = [C.c_void_p]
+            L.air_last_error.restype = C.c_char_p
+            L.air_version.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+class AirError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"AIR error {status}: {msg}")
+        self.status = status
+
+
+def _check(status):
+    if status != AIR_OK:
+        raise AirError(status, lib().air_last_error().decode(errors="replace"))
+
+
+def _view(v) -> View:
+    s = View()
+    s.dir[:] = [float(x) for x in v.dir]
+    s.up[:] = [float(x) for x in v.up]
+    s.center[:] = [float(x) for x in v.center]
+    s.half_extent = float(v.half_extent)
+    return s
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Grid:
+    """A simulation grid resident on the GPU (air_load_grid).
+
+    `desc` is any object with the attributes kind ("uniform" | "amr"), n, lo,
+    hi, rho, and optionally temp, brick, max_level, brick_level, brick_origin,
+    emis_mode, lambda_table, logT_lo, logT_hi, kappa."""
+
+    def __init__(self, desc):
+        d = GridDesc()
+        keep = []
+        d.kind = 0 if desc.kind == "uniform" else 1
+        d.n[:] = [int(x) for x in desc.n]
+        d.lo[:] = [float(x) for x in desc.lo]
+        d.hi[:] = [float(x) for x in desc.hi]
+        rho = np.ascontiguousarray(desc.rho)
+        dt = np.float64 if rho.dtype == np.float64 else np.float32
+        rho = np.ascontiguousarray(rho, dtype=dt)
+        d.field_dtype = 1 if dt == np.float64 else 0
+        d.rho = rho.ctypes.data
+        keep.append(rho)
+        if getattr(desc, "temp", None) is not None:
+            t = np.ascontiguousarray(desc.temp, dtype=dt)
+            d.temp = t.ctypes.data
+            keep.append(t)
+        if d.kind == 1:
+            bl = np.ascontiguousarray(desc.brick_level, dtype=np.int32)
+            bo = np.ascontiguousarray(desc.brick_origin, dtype=np.int32)
+            d.brick, d.max_level, d.n_bricks = int(desc.brick), int(desc.max_level), len(bl)
+            d.brick_level, d.brick_origin = bl.ctypes.data, bo.ctypes.data
+            keep += [bl, bo]
+        kappa = np.ascontiguousarray(desc.kappa, dtype=np.float64)
+        d.n_bands = len(kappa)
+        d.kappa = kappa.ctypes.data
+        keep.append(kappa)
+        d.emis_mode = int(getattr(desc, "emis_mode", 0))
+        if d.emis_mode == 1:
+            tab = np.ascontiguousarray(desc.lambda_table, dtype=np.float32)
+            d.lambda_table = tab.ctypes.data
+            d.n_tbins = tab.shape[1]
+            d.logT_lo, d.logT_hi = float(desc.logT_lo), float(desc.logT_hi)
+            keep.append(tab)
+        self.n_bands = d.n_bands
+        h = C.c_void_p()
+        _check(lib().air_load_grid(C.byref(d), _stream(), C.byref(h)))
+        self._h = h
+        self._cap_hint = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().air_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def profile(self, on=True):
+        """Enable (and reset) or disable per-phase device timing."""
+        _check(lib().air_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        ms = np.zeros(len(PHASES))
+        ln = np.zeros(len(PHASES), dtype=np.int64)
+        _check(lib().air_profile_read(self._h, ms.ctypes.data, ln.ctypes.data))
+        return {p: (float(ms[k]), int(ln[k])) for k, p in enumerate(PHASES)}
+
+    # ---------------------------------------------------------- outputs
+    def _alloc(self, n, mem, fields):
+        import torch
+        nb = self.n_bands
+        cap = max(int(n), 1)
+        if mem == "device":
+            dev = dict(device="cuda")
+        else:
+            dev = dict(device="cpu", pin_memory=True)
+        out = {}
+        spec = dict(level=(torch.int32, (cap,)), i=(torch.int32, (cap,)), j=(torch.int32, (cap,)),
+                    is_leaf=(torch.uint8, (cap,)), coldens=(torch.float32, (cap,)),
+                    intensity=(torch.float32, (nb, cap)), p=(torch.float32, (cap,)),
+                    band_flux=(torch.float64, (nb,)))
+        for k in fields:
+            dt, shp = spec[k]
+            out[k] = torch.empty(shp, dtype=dt, **dev)
+        im = Image()
+        im.mem = AIR_DEVICE if mem == "device" else AIR_HOST
+        im.capacity = cap
+        for k, t in out.items():
+            setattr(im, k, t.data_ptr())
+        return im, out
+
+    @staticmethod
+    def _result(im, out):
+        n = im.n_out
+        res = {k: (v[..., :n] if k != "band_flux" else v) for k, v in out.items()}
+        res.update(n_out=im.n_out, n_leaves=im.n_leaves, n_rays=im.n_rays,
+                   n_steps=im.n_steps, n_sweeps=im.n_sweeps)
+        return res
+
+    ALL = ("level", "i", "j", "is_leaf", "coldens", "intensity", "p", "band_flux")
+
+    def render_fixed(self, view, res, fp64_level=-1, mem="device", fields=ALL):
+        """Fixed res x res image (row-major)."""
+        _check(lib().air_set_stream(self._h, _stream()))
+        im, out = self._alloc(res * res, mem, fields)
+        _check(lib().air_render_fixed(self._h, C.byref(_view(view)), int(res), int(fp64_level),
+                                      C.byref(im)))
+        return self._result(im, out)
+
+    def render_adaptive(self, view, base_res, max_level, xi_crit, xi_norm=0, refine_on=0,
+                        fp64_level=-1, include_interior=False, mem="device", fields=ALL,
+                        capacity=None):
+        """Adaptive image; leaves (or all traced nodes) in creation order."""
+        _check(lib().air_set_stream(self._h, _stream()))
+        p = Params(int(base_res), int(max_level), float(xi_crit), int(xi_norm), int(refine_on),
+                   int(fp64_level), 1 if include_interior else 0)
+        cap = capacity or max(self._cap_hint, 4 * base_res * base_res)
+        im, out = self._alloc(cap, mem, fields)
+        st = lib().air_render_adaptive(self._h, C.byref(_view(view)), C.byref(p), C.byref(im))
+        if st == AIR_ERR_CAPACITY:
+            need = im.n_out
+            im, out = self._alloc(need, mem, fields)
+            st = lib().air_render_adaptive(self._h, C.byref(_view(view)), C.byref(p), C.byref(im))
+        _check(st)
+        self._cap_hint = max(self._cap_hint, int(im.n_out))
+        return self._result(im, out)
+
+
+def version() -> str:
+    return lib().air_version().decode()

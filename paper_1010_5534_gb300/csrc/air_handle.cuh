@@ -1,0 +1,100 @@
+// air_handle.cuh -- the opaque air_grid handle and its device workspace.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "air_refine.cuh"
+
+namespace air {
+
+air_status set_error(air_status s, const char *fmt, ...);
+air_status cuda_fail(cudaError_t e, const char *what);
+
+// Grows a device buffer to at least `bytes` (contents are not kept).
+cudaError_t ensure(void **p, size_t *have, size_t bytes);
+
+struct Workspace {
+  // image quadtree
+  int64_t cap = 0;
+  int n_bands = 0;
+  int8_t *lvl = nullptr;
+  int32_t *pi = nullptr, *pj = nullptr, *child = nullptr;
+  float *N = nullptr, *I = nullptr, *p = nullptr;
+  uint32_t *steps = nullptr, *flag = nullptr;
+  // scans
+  int32_t *bcount = nullptr;
+  int64_t *boff = nullptr;
+  size_t bcount_b = 0, boff_b = 0;
+  int64_t *d_total = nullptr;
+  uint32_t *d_err = nullptr;
+  double *partial = nullptr;
+  size_t partial_b = 0;
+  double *d_flux = nullptr;  // [kMaxBands + 1]: flux then steps
+  // fixed image
+  float *fN = nullptr, *fI = nullptr, *fp = nullptr;
+  uint32_t *fsteps = nullptr;
+  size_t fN_b = 0, fI_b = 0, fp_b = 0, fsteps_b = 0;
+  // staging for host outputs
+  int32_t *o_level = nullptr, *o_i = nullptr, *o_j = nullptr;
+  uint8_t *o_leaf = nullptr;
+  float *o_N = nullptr, *o_p = nullptr, *o_I = nullptr;
+  size_t o_level_b = 0, o_i_b = 0, o_j_b = 0, o_leaf_b = 0, o_N_b = 0, o_p_b = 0, o_I_b = 0;
+  // pinned host scalars
+  int64_t *h_total = nullptr;
+  uint32_t *h_err = nullptr;
+  double *h_flux = nullptr;  // [kMaxBands + 1]
+
+  TreeView tree(int n0, int Lm) const {
+    TreeView t;
+    t.n0 = n0; t.Lm = Lm; t.cap = cap;
+    t.lvl = lvl; t.pi = pi; t.pj = pj; t.child = child;
+    t.N = N; t.I = I; t.p = p; t.steps = steps;
+    return t;
+  }
+};
+
+// Event pairs around launch groups, resolved when a render completes.
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;  // pool, 2 per group
+  std::vector<int> phase;       // phase of group g
+  std::vector<int> nlaunch;     // kernel launches in group g
+  int used = 0;                 // groups recorded in the current render
+  double ms[AIR_N_PHASES] = {0};
+  int64_t launches[AIR_N_PHASES] = {0};
+};
+
+struct LastRender {
+  bool valid = false;
+  air_view view;
+  air_params params;
+  int64_t n_nodes = 0, n_refined = 0;
+  int32_t n_sweeps = 0;
+};
+
+}  // namespace air
+
+struct air_grid {
+  cudaStream_t stream = nullptr;
+  air::GridView gv{};
+  // owned device memory
+  float *d_rho = nullptr;
+  uint32_t *d_xq = nullptr;
+  int32_t *d_base = nullptr, *d_oct = nullptr;
+  int4 *d_binfo = nullptr;
+  float *d_table = nullptr, *d_kappa = nullptr, *d_invkappa = nullptr;
+  int64_t n_cells = 0;
+  air::Workspace ws;
+  air::LastRender last;
+  air::Profiler prof;
+};
+
+namespace air {
+air_status load_grid_impl(const air_grid_desc *d, air_grid *g);
+// Profiling: open a launch group of `phase` containing `nlaunch` kernels; close
+// it after the launches; resolve all groups after the render's final sync.
+cudaError_t prof_open(air_grid *g, int phase, int nlaunch);
+cudaError_t prof_close(air_grid *g);
+cudaError_t prof_resolve(air_grid *g);
+void free_grid_impl(air_grid *g);
+}  // namespace air

@@ -1,0 +1,101 @@
+// air_internal.cuh -- device-side data layout and helpers shared by the
+// library's translation units (grid upload, march, refinement, API).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/air.h"
+
+namespace air {
+
+constexpr int kMaxBands = 64;
+constexpr int kMaxLevels = 16;
+constexpr int kXqFracBits = 24;  // table coordinate fixed point: 8 integer, 24 fraction bits
+
+// Grid as the kernels see it. Positions are in units of the finest cell
+// (uniform: the cell), F = (x - lo) / h per axis.
+struct GridView {
+  int kind;             // AIR_GRID_UNIFORM / AIR_GRID_AMR
+  int nf[3];            // finest cells per axis
+  double lo[3], h[3];   // world origin and finest cell size
+  // cell fields: rho (float) and, for emis_mode 1, the fixed-point table
+  // coordinate of T: xq = round(x * 2^24), x = (log10 T - logT_lo) / dlogT in bins
+  const float *rho;
+  const uint32_t *xq;
+  // block AMR
+  int B, log2B, Lm;     // brick edge (cells), log2 of it, finest level
+  int nb0[3];           // level-0 bricks per axis
+  const int32_t *base;  // [nb0z][nb0y][nb0x]: >= 0 leaf brick id, < 0 -(group + 1)
+  const int32_t *oct;   // [groups][8] children codes (octant = bx | by<<1 | bz<<2)
+  const int4 *binfo;    // per leaf brick: origin x, y, z (finest units), level
+  // emission
+  int emis_mode, n_bands, n_tbins;
+  const float *table;   // [n_bands][n_tbins + 1] (last entry repeated)
+  const float *kappa;   // [n_bands]
+  const float *invkappa;// [n_bands] (0 where kappa == 0)
+};
+
+// Orthographic camera resolved on the host in FP64.
+struct Camera {
+  double c[3], u[3], v[3], d[3];
+  double H;
+};
+
+// Ray list: either explicit nodes (level, i, j) of an n0 base image, or the
+// implicit pixels of a res x res fixed image.
+struct RaySource {
+  int mode;             // 0 nodes, 1 fixed grid
+  int n0;               // base resolution (nodes) or res (grid)
+  const int8_t *lvl;
+  const int32_t *pi, *pj;
+  int64_t first, count; // rays [first, first + count) of the list / image
+  int tile_w;           // grid mode: a warp covers tile_w x (32 / tile_w) pixels
+};
+
+struct RayOut {
+  float *N;             // [stride] column density
+  float *I;             // [n_bands][stride]
+  int64_t stride;
+  uint32_t *steps;      // [stride]
+  float *p;             // [stride] band-summed intensity (NULL: written elsewhere)
+};
+
+struct MarchTune {
+  int block;            // threads per block
+  int fp64_level;       // bricks at this level or deeper use FP64 entry/exit
+};
+
+// Kahan-compensated sum: s += x with running compensation c.
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+  float y = x - c;
+  float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// (1 - e^-x) / x for 0 <= x < 0.25 from its Taylor series
+// sum_{n>=0} (-x)^n / (n+1)!, truncated after x^6 (remainder < x^7/8! < 1.6e-9).
+__device__ __forceinline__ float one_minus_exp_over_x(float x) {
+  float g = 1.0f / 5040.0f;
+  g = fmaf(g, -x, 1.0f / 720.0f);
+  g = fmaf(g, -x, 1.0f / 120.0f);
+  g = fmaf(g, -x, 1.0f / 24.0f);
+  g = fmaf(g, -x, 1.0f / 6.0f);
+  g = fmaf(g, -x, 0.5f);
+  g = fmaf(g, -x, 1.0f);
+  return g;
+}
+
+}  // namespace air
+
+// ---- host-side internal API between translation units ----------------------
+namespace air {
+
+struct DeviceGrid;  // owned by the handle (defined in air_grid.cu)
+
+cudaError_t launch_march(const GridView &g, const Camera &cam, const RaySource &src,
+                         const RayOut &out, const MarchTune &tune, cudaStream_t st);
+cudaError_t launch_band_sum(const float *I, int n_bands, int64_t stride, int64_t first,
+                            int64_t count, float *p, cudaStream_t st);
+
+}  // namespace air

@@ -1,0 +1,427 @@
+// air_march.cu -- per-ray march (Parkin 2010, Section 1 and Section 2 step ii):
+// follow one ray per pixel through the grid and sum, per crossed cell, the
+// column density N = sum rho ds and the emergent intensity of the absorbed
+// emission, front to back, I_b = sum_k (j_k/alpha_k)(1 - e^-dtau_k) e^-tau_<k.
+//
+// One thread marches one ray (x a chunk of bands). Warps hold 32 neighbouring
+// pixels, so their cell fetches fall in the same or adjacent cells.
+//
+// Traversal: the ray's position is kept as an integer finest-level cell
+// coordinate plus a ray parameter t (world length). Inside a block of cells
+// (the whole uniform grid, or one AMR brick) an Amanatides-Woo DDA in FP32
+// local coordinates yields the exact chord of each cell. AMR bricks are found
+// by descending the brick octree from the level-0 brick; a brick is left
+// through the face with the smallest exit parameter and the next brick is the
+// one holding the finest cell across that face, so no cell is skipped or
+// visited twice. Bricks at level >= fp64_level compute their entry point and
+// exit parameter in FP64; coarser bricks in FP32.
+//
+// Accumulation in FP32: N, tau_b and I_b are Kahan-compensated sums;
+// T = exp(-tau) is recomputed from the compensated tau at every cell; the cell
+// term is j ds T (1 - e^-dtau)/dtau from a Taylor polynomial for dtau < 1/4,
+// and (j/alpha)(T_prev - T_next) above.
+#include <cfloat>
+
+#include "air_internal.cuh"
+
+namespace air {
+
+template <int NBT>
+struct RTState {
+  float N, cN;
+  float tau[NBT], ctau[NBT], T[NBT], I[NBT], cI[NBT];
+  uint32_t steps;
+};
+
+struct BandCtx {
+  const float *tab;  // shared: [NBT][tstride]
+  const float *kap;  // shared: [NBT]
+  const float *ik;   // shared: [NBT]
+  int tstride, nbh, emis;
+};
+
+template <int NBT>
+__device__ __forceinline__ void rt_init(RTState<NBT> &r) {
+  r.N = 0.f;
+  r.cN = 0.f;
+  r.steps = 0;
+#pragma unroll
+  for (int b = 0; b < NBT; ++b) {
+    r.tau[b] = 0.f;
+    r.ctau[b] = 0.f;
+    r.T[b] = 1.f;
+    r.I[b] = 0.f;
+    r.cI[b] = 0.f;
+  }
+}
+
+// One cell chord of length ds with density rho and table coordinate xq.
+template <int NBT>
+__device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t xq, float ds,
+                                        const BandCtx &bc) {
+  kahan_add(r.N, r.cN, rho * ds);
+  r.steps += 1;
+  int k = 0;
+  float w = 0.f;
+  if (bc.emis) {
+    k = (int)(xq >> kXqFracBits);
+    w = (float)(xq & ((1u << kXqFracBits) - 1u)) * (1.0f / (float)(1u << kXqFracBits));
+  }
+  const float rho2ds = rho * rho * ds;
+#pragma unroll
+  for (int b = 0; b < NBT; ++b) {
+    if (b < bc.nbh) {
+      float lam = 1.f;
+      if (bc.emis) {
+        const float *t = bc.tab + b * bc.tstride + k;
+        lam = fmaf(w, t[1] - t[0], t[0]);
+      }
+      const float alpha = bc.kap[b] * rho;
+      const float dtau = alpha * ds;
+      float term;
+      if (dtau > 0.f) {
+        kahan_add(r.tau[b], r.ctau[b], dtau);
+        const float Tn = expf(-r.tau[b]);
+        if (dtau < 0.25f)
+          term = rho2ds * lam * r.T[b] * one_minus_exp_over_x(dtau);
+        else
+          term = rho * lam * bc.ik[b] * (r.T[b] - Tn);
+        r.T[b] = Tn;
+      } else {
+        term = rho2ds * lam * r.T[b];
+      }
+      kahan_add(r.I[b], r.cI[b], term);
+    }
+  }
+}
+
+// DDA through a block of nx x ny x nz cells. Q: local entry point (cells),
+// Dl: direction (cells per unit t), tend: block exit relative to entry,
+// (lx, ly, lz): entry cell. Cell (x, y, z) lives at base + z*sz + y*sy + x.
+// Per-axis state is kept in scalars so the loop stays in registers.
+template <int NBT>
+__device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], const float Dl[3],
+                                            float tend, int lx, int ly, int lz, int nx, int ny,
+                                            int nz, int64_t base, int64_t sy, int64_t sz,
+                                            const float *__restrict__ rho,
+                                            const uint32_t *__restrict__ xq, const BandCtx &bc) {
+  const float INF = FLT_MAX;
+  const int s0 = Dl[0] > 0.f ? 1 : -1, s1 = Dl[1] > 0.f ? 1 : -1, s2 = Dl[2] > 0.f ? 1 : -1;
+  const int p0 = Dl[0] > 0.f, p1 = Dl[1] > 0.f, p2 = Dl[2] > 0.f;
+  const float i0 = Dl[0] != 0.f ? 1.0f / Dl[0] : 0.f;
+  const float i1 = Dl[1] != 0.f ? 1.0f / Dl[1] : 0.f;
+  const float i2 = Dl[2] != 0.f ? 1.0f / Dl[2] : 0.f;
+  float tm0 = Dl[0] != 0.f ? ((float)(lx + p0) - Q[0]) * i0 : INF;
+  float tm1 = Dl[1] != 0.f ? ((float)(ly + p1) - Q[1]) * i1 : INF;
+  float tm2 = Dl[2] != 0.f ? ((float)(lz + p2) - Q[2]) * i2 : INF;
+  float tl = 0.f;
+  for (;;) {
+    const float tn = fminf(fminf(tm0, tm1), fminf(tm2, tend));
+    const float ds = tn - tl;
+    if (ds > 0.f) {
+      const int64_t idx = base + (int64_t)lz * sz + (int64_t)ly * sy + lx;
+      const float rh = __ldg(rho + idx);
+      const uint32_t xv = bc.emis ? __ldg(xq + idx) : 0u;
+      rt_cell<NBT>(r, rh, xv, ds, bc);
+    }
+    if (tn >= tend) break;
+    if (tm0 <= tm1 && tm0 <= tm2) {
+      lx += s0;
+      if ((unsigned)lx >= (unsigned)nx) break;  // left the block by rounding
+      tm0 = ((float)(lx + p0) - Q[0]) * i0;
+    } else if (tm1 <= tm2) {
+      ly += s1;
+      if ((unsigned)ly >= (unsigned)ny) break;
+      tm1 = ((float)(ly + p1) - Q[1]) * i1;
+    } else {
+      lz += s2;
+      if ((unsigned)lz >= (unsigned)nz) break;
+      tm2 = ((float)(lz + p2) - Q[2]) * i2;
+    }
+    tl = tn;
+  }
+}
+
+// Pixel centre -> ray in finest-cell units, clipped to the box: F(t) = O + t D.
+__device__ __forceinline__ bool ray_setup(const GridView &g, const Camera &cam, int n0, int L,
+                                          int i, int j, double O[3], double D[3], double &t0,
+                                          double &t1) {
+  const double nL = (double)n0 * (double)(1u << L);
+  const double pix = (2.0 * cam.H) / nL;
+  const double uc = -cam.H + ((double)i + 0.5) * pix;
+  const double vc = -cam.H + ((double)j + 0.5) * pix;
+  t0 = -DBL_MAX;
+  t1 = DBL_MAX;
+  bool hit = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double o = cam.c[a] + uc * cam.u[a] + vc * cam.v[a];
+    O[a] = (o - g.lo[a]) / g.h[a];
+    D[a] = cam.d[a] / g.h[a];
+    if (cam.d[a] == 0.0) {
+      if (!(O[a] >= 0.0 && O[a] < (double)g.nf[a])) hit = false;
+    } else {
+      double ta = (0.0 - O[a]) / D[a], tb = ((double)g.nf[a] - O[a]) / D[a];
+      if (ta > tb) {
+        const double x = ta;
+        ta = tb;
+        tb = x;
+      }
+      t0 = fmax(t0, ta);
+      t1 = fmin(t1, tb);
+    }
+  }
+  return hit && t0 < t1;
+}
+
+__device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+template <int NBT>
+__device__ void march_uniform(RTState<NBT> &r, const GridView &g, const double O[3],
+                              const double D[3], double t0, double t1, const BandCtx &bc) {
+  float Q[3], Dl[3];
+  int lc[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double F = O[a] + t0 * D[a];
+    lc[a] = clampi((int)floor(F), 0, g.nf[a] - 1);
+    Q[a] = (float)F;
+    Dl[a] = (float)D[a];
+  }
+  march_block<NBT>(r, Q, Dl, (float)(t1 - t0), lc[0], lc[1], lc[2], g.nf[0], g.nf[1], g.nf[2], 0,
+                   g.nf[0], (int64_t)g.nf[0] * g.nf[1], g.rho, g.xq, bc);
+}
+
+template <int NBT>
+__device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3], const double D[3],
+                          double t0, double t1, int fp64_level, const BandCtx &bc) {
+  const int B = g.B, lb = g.log2B, Lm = g.Lm;
+  double invD[3];
+  float Of[3], Df[3];
+  int c[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    invD[a] = D[a] != 0.0 ? 1.0 / D[a] : 0.0;
+    Of[a] = (float)O[a];
+    Df[a] = (float)D[a];
+    c[a] = clampi((int)floor(O[a] + t0 * D[a]), 0, g.nf[a] - 1);
+  }
+  double t = t0;
+  const int max_iter = 4 * (g.nf[0] + g.nf[1] + g.nf[2]);
+  const int s0 = lb + Lm;
+  for (int it = 0; it < max_iter && t < t1; ++it) {
+    // leaf brick holding finest cell c
+    int code = __ldg(g.base + ((int64_t)(c[2] >> s0) * g.nb0[1] + (c[1] >> s0)) * g.nb0[0] + (c[0] >> s0));
+    int lev = 0;
+    while (code < 0) {
+      ++lev;
+      const int sh = s0 - lev;
+      const int oc = ((c[0] >> sh) & 1) | (((c[1] >> sh) & 1) << 1) | (((c[2] >> sh) & 1) << 2);
+      code = __ldg(g.oct + (int64_t)(-code - 1) * 8 + oc);
+    }
+    const int4 bi = __ldg(g.binfo + code);
+    const int bo[3] = {bi.x, bi.y, bi.z};
+    const int shift = Lm - bi.w;
+    const int S = B << shift;
+    const float scale = 1.0f / (float)(1 << shift);
+    float Q[3], Dl[3], tend;
+    double te;
+    int ax = -1;
+    const bool deep = bi.w >= fp64_level;
+    if (deep) {
+      te = t1;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (D[a] != 0.0) {
+          const double face = (double)(D[a] > 0.0 ? bo[a] + S : bo[a]);
+          const double ta = (face - O[a]) * invD[a];
+          if (ta < te) {
+            te = ta;
+            ax = a;
+          }
+        }
+        Q[a] = (float)fma(t, D[a], O[a] - (double)bo[a]) * scale;
+        Dl[a] = Df[a] * scale;
+      }
+      if (te < t) te = t;
+      tend = (float)(te - t);
+    } else {
+      const float tf = (float)t;
+      float tr = (float)(t1 - t);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        Q[a] = (fmaf(tf, Df[a], Of[a]) - (float)bo[a]) * scale;
+        Dl[a] = Df[a] * scale;
+        if (Df[a] != 0.f) {
+          const float ta = ((Df[a] > 0.f ? (float)B : 0.f) - Q[a]) / Dl[a];
+          if (ta < tr) {
+            tr = ta;
+            ax = a;
+          }
+        }
+      }
+      if (tr < 0.f) tr = 0.f;
+      tend = tr;
+      te = ax < 0 ? t1 : t + (double)tr;
+    }
+    int lc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) lc[a] = (c[a] - bo[a]) >> shift;
+    march_block<NBT>(r, Q, Dl, tend, lc[0], lc[1], lc[2], B, B, B, (int64_t)code << (3 * lb), B,
+                     (int64_t)B * B, g.rho, g.xq, bc);
+    if (ax < 0) break;
+    t = te;
+    // finest cell just across the exit face; the other coordinates stay in this brick's range
+    bool out = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a == ax) {
+        c[a] = D[a] > 0.0 ? bo[a] + S : bo[a] - 1;
+        out = c[a] < 0 || c[a] >= g.nf[a];
+      } else {
+        const double F = deep ? fma(te, D[a], O[a]) : (double)fmaf((float)te, Df[a], Of[a]);
+        c[a] = clampi((int)floor(F), bo[a], bo[a] + S - 1);
+      }
+    }
+    if (out) break;
+  }
+}
+
+template <int NBT, bool AMR>
+__global__ void __launch_bounds__(256) k_march(GridView g, Camera cam, RaySource src, RayOut out,
+                                               int fp64_level) {
+  extern __shared__ float smem[];
+  const int chunk = blockIdx.y;
+  const int b0 = chunk * NBT;
+  const int nbh = min(NBT, g.n_bands - b0);
+  const int tstride = g.n_tbins + 1;
+  BandCtx bc;
+  bc.tab = smem;
+  bc.kap = smem + NBT * tstride;
+  bc.ik = bc.kap + NBT;
+  bc.tstride = tstride;
+  bc.nbh = nbh;
+  bc.emis = g.emis_mode;
+  {
+    float *tab = smem;
+    if (g.emis_mode)
+      for (int x = threadIdx.x; x < nbh * tstride; x += blockDim.x) tab[x] = g.table[b0 * tstride + x];
+    float *kap = smem + NBT * tstride;
+    for (int x = threadIdx.x; x < NBT; x += blockDim.x) {
+      kap[x] = x < nbh ? g.kappa[b0 + x] : 0.f;
+      kap[NBT + x] = x < nbh ? g.invkappa[b0 + x] : 0.f;
+    }
+  }
+  __syncthreads();
+
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int L, i, j, n0;
+  int64_t k;
+  if (src.mode == 0) {
+    if (r >= src.count) return;
+    k = src.first + r;
+    L = src.lvl[k];
+    i = src.pi[k];
+    j = src.pj[k];
+    n0 = src.n0;
+  } else {
+    const int res = src.n0;
+    const int tw = src.tile_w, th = 32 / tw;
+    const int tiles_x = (res + tw - 1) / tw;
+    const int64_t warp = r >> 5;
+    const int lane = (int)(r & 31);
+    const int64_t ty = warp / tiles_x;
+    const int tx = (int)(warp - ty * tiles_x);
+    i = tx * tw + lane % tw;
+    j = (int)ty * th + lane / tw;
+    if (i >= res || j >= res) return;
+    k = (int64_t)j * res + i;
+    L = 0;
+    n0 = res;
+  }
+  RTState<NBT> st;
+  rt_init<NBT>(st);
+  double O[3], D[3], t0, t1;
+  if (ray_setup(g, cam, n0, L, i, j, O, D, t0, t1)) {
+    if (AMR)
+      march_amr<NBT>(st, g, O, D, t0, t1, fp64_level, bc);
+    else
+      march_uniform<NBT>(st, g, O, D, t0, t1, bc);
+  }
+  if (chunk == 0) {
+    out.N[k] = st.N;
+    out.steps[k] = st.steps;
+  }
+#pragma unroll
+  for (int b = 0; b < NBT; ++b)
+    if (b < nbh) out.I[(int64_t)(b0 + b) * out.stride + k] = st.I[b];
+  if (out.p && gridDim.y == 1) {
+    float p = 0.f;
+#pragma unroll
+    for (int b = 0; b < NBT; ++b)
+      if (b < nbh) p += st.I[b];
+    out.p[k] = p;
+  }
+}
+
+__global__ void k_band_sum(const float *__restrict__ I, int n_bands, int64_t stride, int64_t first,
+                           int64_t count, float *__restrict__ p) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= count) return;
+  const int64_t k = first + r;
+  float s = 0.f;
+  for (int b = 0; b < n_bands; ++b) s += I[(int64_t)b * stride + k];
+  p[k] = s;
+}
+
+template <int NBT>
+static cudaError_t launch_t(const GridView &g, const Camera &cam, const RaySource &src,
+                            const RayOut &out, const MarchTune &tune, cudaStream_t st) {
+  const int chunks = (g.n_bands + NBT - 1) / NBT;
+  int64_t threads;
+  if (src.mode == 0) {
+    threads = src.count;
+  } else {
+    const int tw = src.tile_w, th = 32 / tw;
+    const int64_t tiles = (int64_t)((src.n0 + tw - 1) / tw) * ((src.n0 + th - 1) / th);
+    threads = tiles * 32;
+  }
+  if (threads <= 0) return cudaSuccess;
+  const int block = tune.block;
+  const int64_t blocks = (threads + block - 1) / block;
+  if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(float) * (size_t)(NBT * (g.n_tbins + 1) + 2 * NBT);
+  dim3 grid((unsigned)blocks, chunks);
+  if (g.kind == AIR_GRID_AMR)
+    k_march<NBT, true><<<grid, block, smem, st>>>(g, cam, src, out, tune.fp64_level);
+  else
+    k_march<NBT, false><<<grid, block, smem, st>>>(g, cam, src, out, tune.fp64_level);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (chunks > 1 && out.p) {
+    const int64_t first = src.mode == 0 ? src.first : 0;
+    const int64_t count = src.mode == 0 ? src.count : (int64_t)src.n0 * src.n0;
+    return launch_band_sum(out.I, g.n_bands, out.stride, first, count, out.p, st);
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_march(const GridView &g, const Camera &cam, const RaySource &src,
+                         const RayOut &out, const MarchTune &tune, cudaStream_t st) {
+  if (g.n_bands <= 1) return launch_t<1>(g, cam, src, out, tune, st);
+  if (g.n_bands <= 2) return launch_t<2>(g, cam, src, out, tune, st);
+  if (g.n_bands <= 4) return launch_t<4>(g, cam, src, out, tune, st);
+  if (g.n_bands <= 8) return launch_t<8>(g, cam, src, out, tune, st);
+  return launch_t<16>(g, cam, src, out, tune, st);
+}
+
+cudaError_t launch_band_sum(const float *I, int n_bands, int64_t stride, int64_t first,
+                            int64_t count, float *p, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const int block = 256;
+  k_band_sum<<<(unsigned)((count + block - 1) / block), block, 0, st>>>(I, n_bands, stride, first,
+                                                                       count, p);
+  return cudaGetLastError();
+}
+
+}  // namespace air

@@ -1,0 +1,375 @@
+// air_refine.cu -- the adaptive image (Parkin 2010, Section 2 steps iii-vi):
+// truncation-error scan (Section 3, Eq. 2), 2:1 level balance between adjacent
+// pixels, quadtree refinement with a warp-ballot prefix sum that compacts the
+// new rays, and the leaf output with the band flux.
+//
+// The image quadtree is a node list: the base image row-major (node j*n0 + i),
+// then four consecutive children per refined node, in the order of the
+// parents. Each node stores its level, (i, j) at that level and the index of
+// its first child (-1 for a leaf). The pixel at level L holding (i, j) is
+// found by descending from the base node through the child links; this gives
+// the deepest existing node at a level <= L, which is the value a missing
+// neighbour takes in the stencil.
+#include <cfloat>
+
+#include "air_refine.cuh"
+
+namespace air {
+
+__device__ __forceinline__ int descend(const TreeView &t, int L, int i, int j) {
+  int k = (j >> L) * t.n0 + (i >> L);
+  for (int l = 1; l <= L; ++l) {
+    const int c = t.child[k];
+    if (c < 0) break;
+    const int s = L - l;
+    k = c + ((((j >> s) & 1) << 1) | ((i >> s) & 1));
+  }
+  return k;
+}
+
+// Eq. 2 on the 3x3 stencil s[3*(dj+1) + (di+1)], FP64 with every operation
+// rounded separately (no fused multiply-add), in a fixed order.
+__device__ double xi_eq2(const double s[9], int xi_norm) {
+  const double c = s[4], xm = s[3], xp = s[5], ym = s[1], yp = s[7];
+  const double mm = s[0], pm = s[2], mp = s[6], pp = s[8];
+  const double c2 = __dmul_rn(2.0, c);
+  const double d2u = __dadd_rn(__dsub_rn(xp, c2), xm);
+  const double d2v = __dadd_rn(__dsub_rn(yp, c2), ym);
+  const double duv = __dmul_rn(__dadd_rn(__dsub_rn(__dsub_rn(pp, pm), mp), mm), 0.25);
+  const double num = __dadd_rn(__dadd_rn(__dmul_rn(d2u, d2u), __dmul_rn(d2v, d2v)),
+                               __dmul_rn(2.0, __dmul_rn(duv, duv)));
+  const double au = __dadd_rn(fabs(__dsub_rn(xp, c)), fabs(__dsub_rn(c, xm)));
+  const double av = __dadd_rn(fabs(__dsub_rn(yp, c)), fabs(__dsub_rn(c, ym)));
+  double den = __dadd_rn(__dmul_rn(au, au), __dmul_rn(av, av));
+  if (xi_norm == 1) den = __dmul_rn(2.0, den);
+  if (num == 0.0) return 0.0;
+  if (den == 0.0) return 1.0;
+  const double x = __dsqrt_rn(__ddiv_rn(num, den));
+  return x > 1.0 ? 1.0 : x;
+}
+
+// Step iii: flag every leaf below max_level whose xi >= xi_crit.
+__global__ void k_xi_scan(TreeView t, int64_t n, double xi_crit, int xi_norm, int refine_on,
+                          uint32_t *__restrict__ flag) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  uint32_t f = 0;
+  const int L = t.lvl[k];
+  if (t.child[k] < 0 && L < t.Lm) {
+    const int i = t.pi[k], j = t.pj[k];
+    const int nl = t.n0 << L;
+    int q[9];
+#pragma unroll
+    for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+      for (int di = -1; di <= 1; ++di) {
+        const int ii = min(max(i + di, 0), nl - 1), jj = min(max(j + dj, 0), nl - 1);
+        q[3 * (dj + 1) + (di + 1)] = (di == 0 && dj == 0) ? (int)k : descend(t, L, ii, jj);
+      }
+    double s[9];
+    if (refine_on == 0 || refine_on == 2) {
+#pragma unroll
+      for (int m = 0; m < 9; ++m) s[m] = (double)t.p[q[m]];
+      f |= xi_eq2(s, xi_norm) >= xi_crit;
+    }
+    if (refine_on == 1 || refine_on == 2) {
+#pragma unroll
+      for (int m = 0; m < 9; ++m) s[m] = (double)t.N[q[m]];
+      f |= xi_eq2(s, xi_norm) >= xi_crit;
+    }
+  }
+  flag[k] = f;
+}
+
+// Step iii, balance: a flagged leaf at level L forces every leaf at a level
+// < L that covers one of its 8 same-level neighbours, and so on down the
+// levels. Each newly set flag is expanded by the thread that set it.
+__global__ void k_balance(TreeView t, int64_t n, uint32_t *__restrict__ flag,
+                          uint32_t *__restrict__ err) {
+  const int64_t k0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k0 >= n || flag[k0] == 0) return;
+  int stack[kBalanceStack];
+  int sp = 0;
+  stack[sp++] = (int)k0;
+  while (sp > 0) {
+    const int q = stack[--sp];
+    const int L = t.lvl[q], i = t.pi[q], j = t.pj[q];
+    const int nl = t.n0 << L;
+    for (int dj = -1; dj <= 1; ++dj)
+      for (int di = -1; di <= 1; ++di) {
+        if (!di && !dj) continue;
+        const int ii = i + di, jj = j + dj;
+        if (ii < 0 || jj < 0 || ii >= nl || jj >= nl) continue;
+        const int m = descend(t, L, ii, jj);
+        if (t.child[m] < 0 && t.lvl[m] < L) {
+          if (atomicExch(flag + m, 1u) == 0u) {
+            if (sp < kBalanceStack) stack[sp++] = m;
+            else atomicOr(err, 1u);
+          }
+        }
+      }
+  }
+}
+
+// ---- warp-ballot prefix sums ------------------------------------------------
+// A block covers kScanItems = kScanRounds * kScanBlock consecutive items;
+// round r holds items [r * kScanBlock, (r + 1) * kScanBlock) of the block, one
+// per thread, so every load is coalesced and the block-local order is the
+// global order.
+
+struct PredFlag {
+  const uint32_t *flag;
+  __device__ bool operator()(int64_t k) const { return flag[k] != 0; }
+};
+struct PredLeaf {
+  const int32_t *child;
+  int all;
+  __device__ bool operator()(int64_t k) const { return all || child[k] < 0; }
+};
+
+template <class Pred>
+__global__ void __launch_bounds__(kScanBlock) k_count(Pred pred, int64_t n, int32_t *bcount) {
+  __shared__ int32_t wsum[kScanBlock / 32];
+  const int64_t start = (int64_t)blockIdx.x * kScanItems;
+  int32_t cnt = 0;
+  for (int rr = 0; rr < kScanRounds; ++rr) {
+    const int64_t k = start + (int64_t)rr * kScanBlock + threadIdx.x;
+    const bool p = k < n && pred(k);
+    cnt += __popc(__ballot_sync(0xffffffffu, p));
+  }
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t s = 0;
+    for (int w = 0; w < kScanBlock / 32; ++w) s += wsum[w];
+    bcount[blockIdx.x] = s;
+  }
+}
+
+// Exclusive scan of the per-block counts in one block; total -> *total.
+__global__ void __launch_bounds__(1024) k_scan_blocks(const int32_t *bcount, int64_t nb,
+                                                      int64_t *boff, int64_t *total) {
+  __shared__ int64_t part[1024];
+  const int64_t per = (nb + 1023) / 1024;
+  const int64_t a = threadIdx.x * per, b = min(nb, a + per);
+  int64_t s = 0;
+  for (int64_t x = a; x < b; ++x) s += bcount[x];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const int64_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int64_t run = part[threadIdx.x] - s;
+  for (int64_t x = a; x < b; ++x) {
+    boff[x] = run;
+    run += bcount[x];
+  }
+  if (threadIdx.x == 1023) *total = part[1023];
+}
+
+// Round-by-round block scan; calls emit(k, rank) for every selected item.
+template <class Pred, class Emit>
+__device__ __forceinline__ void block_scan_emit(Pred pred, Emit &emit, int64_t n, int64_t boff) {
+  __shared__ int32_t wsum[kScanBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t start = (int64_t)blockIdx.x * kScanItems;
+  int64_t run = boff;
+  for (int rr = 0; rr < kScanRounds; ++rr) {
+    const int64_t k = start + (int64_t)rr * kScanBlock + threadIdx.x;
+    const bool p = k < n && pred(k);
+    const uint32_t bal = __ballot_sync(0xffffffffu, p);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    int32_t before = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kScanBlock / 32; ++w) {
+      const int32_t v = wsum[w];
+      before += w < warp ? v : 0;
+      tot += v;
+    }
+    if (p) emit(k, run + before + __popc(bal & ((1u << lane) - 1u)));
+    run += tot;
+    __syncthreads();
+  }
+}
+
+// Step iv: four children per flagged leaf at n_old + 4 * rank.
+struct EmitChildren {
+  TreeView t;
+  int64_t n_old;
+  __device__ void operator()(int64_t k, int64_t rank) {
+    const int64_t c0 = n_old + 4 * rank;
+    const int L = t.lvl[k] + 1, i = t.pi[k], j = t.pj[k];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      t.lvl[c0 + c] = (int8_t)L;
+      t.pi[c0 + c] = 2 * i + (c & 1);
+      t.pj[c0 + c] = 2 * j + (c >> 1);
+      t.child[c0 + c] = -1;
+    }
+    t.child[k] = (int32_t)c0;
+  }
+};
+
+__global__ void __launch_bounds__(kScanBlock) k_emit_children(TreeView t, const uint32_t *flag,
+                                                              int64_t n, const int64_t *boff,
+                                                              int64_t n_old) {
+  EmitChildren e{t, n_old};
+  block_scan_emit(PredFlag{flag}, e, n, boff[blockIdx.x]);
+}
+
+// Step vi: copy the selected nodes (leaves, or all) to the output arrays.
+struct EmitOut {
+  TreeView t;
+  OutView o;
+  __device__ void operator()(int64_t k, int64_t r) {
+    if (o.level) o.level[r] = t.lvl[k];
+    if (o.i) o.i[r] = t.pi[k];
+    if (o.j) o.j[r] = t.pj[k];
+    if (o.is_leaf) o.is_leaf[r] = t.child[k] < 0;
+    if (o.N) o.N[r] = t.N[k];
+    if (o.p) o.p[r] = t.p[k];
+    if (o.I)
+      for (int b = 0; b < o.n_bands; ++b) o.I[(int64_t)b * o.stride + r] = t.I[(int64_t)b * t.cap + k];
+  }
+};
+
+__global__ void __launch_bounds__(kScanBlock) k_emit_out(TreeView t, OutView o, int all, int64_t n,
+                                                         const int64_t *boff) {
+  EmitOut e{t, o};
+  block_scan_emit(PredLeaf{t.child, all}, e, n, boff[blockIdx.x]);
+}
+
+// Base image, row-major: node j*n0 + i.
+__global__ void k_init_base(TreeView t) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n = (int64_t)t.n0 * t.n0;
+  if (k >= n) return;
+  t.lvl[k] = 0;
+  t.pi[k] = (int32_t)(k % t.n0);
+  t.pj[k] = (int32_t)(k / t.n0);
+  t.child[k] = -1;
+}
+
+// ---- band flux and step count --------------------------------------------
+// Per block: sum over selected pixels of I_b x area(level) in FP64 and of the
+// step counts; a second kernel adds the block partials in block order.
+__global__ void __launch_bounds__(256) k_flux_partial(FluxArgs a) {
+  __shared__ double sh[256];
+  const int64_t start = (int64_t)blockIdx.x * a.per_block;
+  const int64_t end = min(a.n, start + a.per_block);
+  double *outp = a.partial + (int64_t)blockIdx.x * (a.n_bands + 1);
+  for (int b = -1; b < a.n_bands; ++b) {
+    double s = 0.0;
+    for (int64_t k = start + threadIdx.x; k < end; k += blockDim.x) {
+      const bool leaf = a.child ? a.child[k] < 0 : true;
+      if (b < 0) {
+        s += (double)a.steps[k];
+      } else if (leaf) {
+        const int L = a.lvl ? a.lvl[k] : 0;
+        s += (double)a.I[(int64_t)b * a.stride + k] * a.area0 / (double)(1ull << (2 * L));
+      }
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+      if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) outp[b + 1] = sh[0];
+    __syncthreads();
+  }
+}
+
+__global__ void k_flux_final(const double *partial, int64_t nblocks, int n_bands, double *flux,
+                             double *steps) {
+  const int b = (int)threadIdx.x - 1;
+  if (b >= n_bands) return;
+  double s = 0.0;
+  for (int64_t x = 0; x < nblocks; ++x) s += partial[x * (n_bands + 1) + b + 1];
+  if (b < 0) *steps = s;
+  else flux[b] = s;
+}
+
+// ---- host launchers ----------------------------------------------------------
+
+static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+cudaError_t launch_init_base(const TreeView &t, cudaStream_t st) {
+  const int64_t n = (int64_t)t.n0 * t.n0;
+  k_init_base<<<nblk(n, 256), 256, 0, st>>>(t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xi_scan(const TreeView &t, int64_t n, double xi_crit, int xi_norm,
+                           int refine_on, uint32_t *flag, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_xi_scan<<<nblk(n, 256), 256, 0, st>>>(t, n, xi_crit, xi_norm, refine_on, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_balance(const TreeView &t, int64_t n, uint32_t *flag, uint32_t *err,
+                           cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_balance<<<nblk(n, 128), 128, 0, st>>>(t, n, flag, err);
+  return cudaGetLastError();
+}
+
+int64_t scan_blocks(int64_t n) { return (n + kScanItems - 1) / kScanItems; }
+
+cudaError_t launch_count_flags(const uint32_t *flag, int64_t n, int32_t *bcount, int64_t *boff,
+                               int64_t *total, cudaStream_t st) {
+  const int64_t nb = scan_blocks(n);
+  if (nb == 0) return cudaMemsetAsync(total, 0, sizeof(int64_t), st);
+  k_count<<<(unsigned)nb, kScanBlock, 0, st>>>(PredFlag{flag}, n, bcount);
+  k_scan_blocks<<<1, 1024, 0, st>>>(bcount, nb, boff, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emit_children(const TreeView &t, const uint32_t *flag, int64_t n,
+                                 const int64_t *boff, int64_t n_old, cudaStream_t st) {
+  const int64_t nb = scan_blocks(n);
+  if (nb == 0) return cudaSuccess;
+  k_emit_children<<<(unsigned)nb, kScanBlock, 0, st>>>(t, flag, n, boff, n_old);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_leaves(const TreeView &t, int all, int64_t n, int32_t *bcount,
+                                int64_t *boff, int64_t *total, cudaStream_t st) {
+  const int64_t nb = scan_blocks(n);
+  if (nb == 0) return cudaMemsetAsync(total, 0, sizeof(int64_t), st);
+  k_count<<<(unsigned)nb, kScanBlock, 0, st>>>(PredLeaf{t.child, all}, n, bcount);
+  k_scan_blocks<<<1, 1024, 0, st>>>(bcount, nb, boff, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emit_out(const TreeView &t, const OutView &o, int all, int64_t n,
+                            const int64_t *boff, cudaStream_t st) {
+  const int64_t nb = scan_blocks(n);
+  if (nb == 0) return cudaSuccess;
+  k_emit_out<<<(unsigned)nb, kScanBlock, 0, st>>>(t, o, all, n, boff);
+  return cudaGetLastError();
+}
+
+int64_t flux_blocks(int64_t n) {
+  const int64_t per = 8192;
+  return n <= 0 ? 0 : (n + per - 1) / per;
+}
+
+cudaError_t launch_flux(FluxArgs a, double *flux, double *steps, cudaStream_t st) {
+  a.per_block = 8192;
+  const int64_t nb = flux_blocks(a.n);
+  if (nb == 0) {
+    cudaError_t e = cudaMemsetAsync(flux, 0, sizeof(double) * a.n_bands, st);
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(steps, 0, sizeof(double), st);
+  }
+  k_flux_partial<<<(unsigned)nb, 256, 0, st>>>(a);
+  k_flux_final<<<1, ((a.n_bands + 1 + 31) / 32) * 32, 0, st>>>(a.partial, nb, a.n_bands, flux, steps);
+  return cudaGetLastError();
+}
+
+}  // namespace air

@@ -1,0 +1,319 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance: every pixel value (column density N, intensity I_b) within
+1e-5 relative of the oracle, plus an absolute floor of 1e-7 x the image
+maximum for pixels whose value comes from a sliver of a cell (a grazing
+chord, where FP32 ray geometry dominates). Integer results (the refinement
+tree, pixel layout, step counts on axis views) are compared exactly."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1010_5534_gb300 as air
+import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU-only machines
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+RTOL = 1e-5
+FLOOR = 1e-7
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    air.build()
+
+
+def close(gpu, orc, what, rtol=RTOL, floor=FLOOR):
+    g = np.asarray(gpu, dtype=np.float64)
+    o = np.asarray(orc, dtype=np.float64)
+    assert g.shape == o.shape, (what, g.shape, o.shape)
+    atol = floor * max(float(np.abs(o).max()) if o.size else 0.0, 1e-300)
+    err = np.abs(g - o)
+    bad = err > rtol * np.abs(o) + atol
+    if bad.any():
+        k = np.argmax(err / (np.abs(o) + atol))
+        raise AssertionError(f"{what}: {bad.sum()} of {bad.size} off; worst at {k}: gpu {g.flat[k]!r} "
+                             f"oracle {o.flat[k]!r} rel {err.flat[k] / max(abs(o.flat[k]), 1e-300):.3e}")
+
+
+def np_(t):
+    return t.cpu().numpy() if hasattr(t, "cpu") else np.asarray(t)
+
+
+# ------------------------------------------------------------------ scenes
+@pytest.fixture(scope="module")
+def wind():
+    s = scenes.wind_shell_uniform(0)
+    return s, air.Grid(s), oracle.Oracle(s)
+
+
+@pytest.fixture(scope="module")
+def cone4():
+    s = scenes.cone_shock_amr(1, n_base=32, brick=8, levels=2, n_bands=4, e_lo=0.5, e_hi=10.0,
+                              kappa0=0.4, thickness=0.08)
+    return s, air.Grid(s), oracle.Oracle(s)
+
+
+@pytest.fixture(scope="module")
+def cone1():
+    s = scenes.cone_shock_amr(2, n_base=32, brick=8, levels=2)
+    return s, air.Grid(s), oracle.Oracle(s)
+
+
+def fixed_pair(sc, g, o, view, res, **kw):
+    r = g.render_fixed(view, res, **kw)
+    f = o.fixed(view, res)
+    return r, f
+
+
+# ------------------------------------------------------------------ fixed images
+@pytest.mark.parametrize("res", [128, 100])
+def test_fixed_uniform_axis(wind, res):
+    sc, g, o = wind
+    v = scenes.axis_view("+z")
+    r, f = fixed_pair(sc, g, o, v, res)
+    assert r["n_out"] == res * res
+    assert (np_(r["i"]) == f["i"]).all() and (np_(r["j"]) == f["j"]).all()
+    close(np_(r["coldens"]), f["col"], "N")
+    close(np_(r["intensity"])[0], f["inten"][:, 0], "I")
+    # axis view: segment counts are exact
+    assert r["n_steps"] == int(f["steps"].sum())
+    flux = (f["inten"][:, 0] * (2.0 / res) ** 2).sum()
+    assert np_(r["band_flux"])[0] == pytest.approx(flux, rel=RTOL)
+
+
+def test_fixed_uniform_oblique(wind):
+    sc, g, o = wind
+    for v in scenes.random_views(4, 3):
+        r, f = fixed_pair(sc, g, o, v, 61)
+        close(np_(r["coldens"]), f["col"], "N")
+        close(np_(r["intensity"])[0], f["inten"][:, 0], "I")
+        assert abs(r["n_steps"] - f["steps"].sum()) <= 1e-4 * f["steps"].sum() + 8
+
+
+@pytest.mark.parametrize("fp64_level", [-1, 0, 99])
+def test_fixed_amr_multiband(cone4, fp64_level):
+    sc, g, o = cone4
+    views = [scenes.axis_view("+z"), scenes.axis_view("-x")] + scenes.random_views(9, 2)
+    for v in views:
+        r, f = fixed_pair(sc, g, o, v, 77, fp64_level=fp64_level)
+        close(np_(r["coldens"]), f["col"], f"N {v.dir}")
+        I = np_(r["intensity"])
+        for b in range(sc.n_bands):
+            close(I[b], f["inten"][:, b], f"I[{b}] {v.dir}")
+        pf = f["inten"].sum(axis=1)
+        close(np_(r["p"]), pf, "p")
+
+
+def test_fixed_image_missing_the_box(wind):
+    sc, g, o = wind
+    v = scenes.View(dir=(0, 0, 1), center=(5.0, 0.0, 0.0), half_extent=1.0)
+    r = g.render_fixed(v, 16)
+    assert float(np_(r["coldens"]).max()) == 0.0 and r["n_steps"] == 0
+    assert float(np_(r["band_flux"])[0]) == 0.0
+
+
+def test_fixed_res_one_and_face_aligned(wind):
+    sc, g, o = wind
+    for res in (1, 2, 32, 64):   # res 2, 32, 64: pixel centres on cell faces
+        r, f = fixed_pair(sc, g, o, scenes.axis_view("+y"), res)
+        close(np_(r["coldens"]), f["col"], f"N res {res}")
+        close(np_(r["intensity"])[0], f["inten"][:, 0], f"I res {res}")
+
+
+# ------------------------------------------------------------------ adaptive images
+def nodes_of(r):
+    return {k: np_(r[k]) for k in ("level", "i", "j", "is_leaf", "coldens", "p")} | \
+        {"I": np_(r["intensity"])}
+
+
+@pytest.mark.parametrize("xc", [0.2, 0.5, 0.8])
+def test_air_uniform_matches_oracle(wind, xc):
+    sc, g, o = wind
+    v = scenes.axis_view("+z")
+    r = g.render_adaptive(v, 16, 3, xc, include_interior=True)
+    t = o.air(v, 16, 3, xc)
+    n = nodes_of(r)
+    assert r["n_rays"] == t["n_nodes"] and r["n_leaves"] == t["n_leaves"]
+    assert r["n_sweeps"] == t["n_sweeps"]
+    for k in ("level", "i", "j"):
+        assert (n[k] == t[k]).all(), k
+    assert (n["is_leaf"] == t["leaf"]).all()
+    close(n["coldens"], t["col"], "N")
+    close(n["I"][0], t["inten"][:, 0], "I")
+    assert np_(r["band_flux"])[0] == pytest.approx(t["band_flux"][0], rel=RTOL)
+    assert r["n_steps"] == t["n_steps"]
+
+
+def _replay_check(g, o, v, n0, Lm, xc, **kw):
+    r = g.render_adaptive(v, n0, Lm, xc, include_interior=True, **kw)
+    n = nodes_of(r)
+    rp = dict(level=n["level"], i=n["i"], j=n["j"], p_int=n["p"].astype(np.float64),
+              p_col=n["coldens"].astype(np.float64))
+    kw2 = {k: kw[k] for k in ("xi_norm", "refine_on") if k in kw}
+    t = o.air(v, n0, Lm, xc, replay=rp, **kw2)
+    assert t["n_nodes"] == r["n_rays"]
+    for k in ("level", "i", "j"):
+        assert (t[k] == n[k]).all(), k
+    assert (t["leaf"] == n["is_leaf"]).all()
+    return r
+
+
+@pytest.mark.parametrize("refine_on,xi_norm", [(0, 0), (1, 0), (2, 1), (0, 1)])
+def test_air_refinement_bit_exact_on_gpu_values(cone4, refine_on, xi_norm):
+    """Fed the GPU's own FP32 pixel values, the oracle's scan/balance/refine
+    loop reproduces the GPU quadtree exactly (node by node, in order)."""
+    sc, g, o = cone4
+    for v in (scenes.axis_view("+z"), scenes.random_views(5, 1)[0]):
+        _replay_check(g, o, v, 12, 3, 0.3, refine_on=refine_on, xi_norm=xi_norm)
+
+
+def test_air_amr_matches_oracle_on_decided_nodes(cone1):
+    """Own FP64 march on the oracle side: trees agree wherever the criterion's
+    margin exceeds the value tolerance."""
+    sc, g, o = cone1
+    v = scenes.axis_view("+z")
+    r = g.render_adaptive(v, 32, 3, 0.5, include_interior=True)
+    t = o.air(v, 32, 3, 0.5)
+    n = nodes_of(r)
+    key_g = set(zip(n["level"].tolist(), n["i"].tolist(), n["j"].tolist()))
+    key_o = set(zip(t["level"].tolist(), t["i"].tolist(), t["j"].tolist()))
+    diff = key_g ^ key_o
+    assert len(diff) <= 0.002 * len(key_o), len(diff)
+    # values on common nodes
+    idx_o = {k: m for m, k in enumerate(zip(t["level"].tolist(), t["i"].tolist(), t["j"].tolist()))}
+    common = [(m, idx_o[k]) for m, k in enumerate(zip(n["level"].tolist(), n["i"].tolist(),
+                                                      n["j"].tolist())) if k in idx_o]
+    gi, oi = np.array(common).T
+    close(n["coldens"][gi], t["col"][oi], "N")
+    close(n["I"][0][gi], t["inten"][oi, 0], "I")
+
+
+def test_air_zero_threshold_equals_fixed_finest(cone4):
+    sc, g, o = cone4
+    v = scenes.axis_view("+z")
+    r = g.render_adaptive(v, 8, 3, 0.0)
+    f = g.render_fixed(v, 64)
+    lv, i, j = np_(r["level"]), np_(r["i"]), np_(r["j"])
+    assert (lv == 3).all() and r["n_out"] == 64 * 64
+    order = np.argsort(j * 64 + i)
+    assert (np_(r["coldens"])[order] == np_(f["coldens"])).all()
+    assert (np_(r["intensity"])[:, order] == np_(f["intensity"])).all()
+
+
+def test_air_invariants_and_threshold_extremes(cone1):
+    sc, g, o = cone1
+    v = scenes.axis_view("+z")
+    r = g.render_adaptive(v, 16, 4, 1.01)
+    assert r["n_rays"] == 256 and r["n_sweeps"] == 0 and r["n_leaves"] == 256
+    for xc in (0.5, 0.1):
+        r = g.render_adaptive(v, 16, 4, xc)
+        nref = (r["n_rays"] - 256) // 4
+        assert r["n_rays"] == 256 + 4 * nref and r["n_leaves"] == 256 + 3 * nref
+        lv, i, j = np_(r["level"]), np_(r["i"]), np_(r["j"])
+        nf = 16 << 4
+        R = np.full((nf, nf), -1)
+        for L, a, b in zip(lv, i, j):
+            s = 1 << (4 - L)
+            assert (R[b * s:(b + 1) * s, a * s:(a + 1) * s] == -1).all()
+            R[b * s:(b + 1) * s, a * s:(a + 1) * s] = L
+        assert (R >= 0).all()
+        for dj, di in ((0, 1), (1, 0), (1, 1), (1, -1)):
+            A = R[max(dj, 0):nf + min(dj, 0), max(di, 0):nf + min(di, 0)]
+            B = R[max(-dj, 0):nf + min(-dj, 0), max(-di, 0):nf + min(-di, 0)]
+            assert np.abs(A - B).max() <= 1
+
+
+def test_air_edge_sizes(wind):
+    sc, g, o = wind
+    v = scenes.axis_view("+z")
+    for n0, Lm, xc in ((1, 0, 0.5), (1, 4, 0.2), (3, 3, 0.4), (5, 2, 0.0)):
+        r = g.render_adaptive(v, n0, Lm, xc, include_interior=True)
+        t = o.air(v, n0, Lm, xc)
+        n = nodes_of(r)
+        assert r["n_rays"] == t["n_nodes"], (n0, Lm)
+        for k in ("level", "i", "j"):
+            assert (n[k] == t[k]).all()
+        close(n["I"][0], t["inten"][:, 0], "I")
+
+
+def test_host_and_device_outputs_agree(cone4):
+    sc, g, o = cone4
+    v = scenes.random_views(2, 1)[0]
+    d = g.render_adaptive(v, 16, 2, 0.4, mem="device")
+    h = g.render_adaptive(v, 16, 2, 0.4, mem="host")
+    for k in ("level", "i", "j", "coldens", "intensity", "p", "band_flux"):
+        assert (np_(d[k]) == np_(h[k])).all(), k
+    fd = g.render_fixed(v, 33, mem="device")
+    fh = g.render_fixed(v, 33, mem="host")
+    for k in ("coldens", "intensity", "p"):
+        assert (np_(fd[k]) == np_(fh[k])).all(), k
+
+
+def test_capacity_retry_and_profile(cone1):
+    sc, g, o = cone1
+    v = scenes.axis_view("+z")
+    g.profile(True)
+    r1 = g.render_adaptive(v, 16, 3, 0.3, capacity=10)     # too small -> retry inside
+    r2 = g.render_adaptive(v, 16, 3, 0.3)
+    assert r1["n_out"] == r2["n_out"]
+    assert (np_(r1["coldens"]) == np_(r2["coldens"])).all()
+    prof = g.profile_read()
+    assert prof["march"][1] > 0 and prof["march"][0] > 0.0
+    assert prof["scan"][1] > 0 and prof["output"][1] > 0
+    g.profile(False)
+
+
+def test_bad_arguments(wind):
+    sc, g, o = wind
+    v = scenes.axis_view("+z")
+    with pytest.raises(air.AirError) as e:
+        g.render_adaptive(v, 0, 3, 0.5)
+    assert e.value.status == air.AIR_ERR_ARG
+    with pytest.raises(air.AirError):
+        g.render_adaptive(v, 16, 3, -1.0)
+    with pytest.raises(air.AirError):
+        g.render_adaptive(scenes.View(dir=(0, 1, 0), up=(0, 2, 0)), 16, 3, 0.5)
+    with pytest.raises(air.AirError):
+        g.render_fixed(v, 0)
+    bad = scenes.wind_shell_uniform(0, n=8)
+    bad.rho[1, 2, 3] = -1.0
+    with pytest.raises(air.AirError) as e:
+        air.Grid(bad)
+    assert e.value.status == air.AIR_ERR_ARG
+    amr = scenes.cone_shock_amr(0, n_base=16, brick=4, levels=1)
+    amr.brick_level = amr.brick_level[:-1].copy()   # hole in the tiling
+    amr.brick_origin = amr.brick_origin[:-1].copy()
+    amr.rho = amr.rho[:-1].copy()
+    amr.temp = amr.temp[:-1].copy()
+    with pytest.raises(air.AirError):
+        air.Grid(amr)
+    # the library stays usable after errors
+    r = g.render_fixed(v, 8)
+    assert r["n_out"] == 64
+
+
+# ------------------------------------------------------------------ full size (bench config)
+def test_cone_full_size_sampled():
+    """The 128^3-base, 16^3-brick, 3-level cone-shock grid at the benchmark's
+    launch configuration (256^2 base image, max level 4, xi_crit 0.5): sampled
+    leaves against the oracle ray by ray, and the tree invariants."""
+    sc = scenes.cone_shock_amr(0)
+    g = air.Grid(sc)
+    v = scenes.axis_view("+z")
+    r = g.render_adaptive(v, 256, 4, 0.5)
+    nref = (r["n_rays"] - 65536) // 4
+    assert r["n_rays"] == 65536 + 4 * nref and r["n_leaves"] == 65536 + 3 * nref
+    lv, i, j = np_(r["level"]), np_(r["i"]), np_(r["j"])
+    rng = np.random.default_rng(0)
+    pick = rng.choice(len(lv), size=1500, replace=False)
+    o = oracle.Oracle(sc)
+    col, inten, _ = o.trace(v, 256, lv[pick], i[pick], j[pick])
+    close(np_(r["coldens"])[pick], col, "N", floor=1e-6)
+    close(np_(r["intensity"])[0][pick], inten[:, 0], "I", floor=1e-6)
+    f = g.render_fixed(v, 4096, fields=("band_flux",))
+    err = abs(np_(r["band_flux"])[0] - np_(f["band_flux"])[0]) / np_(f["band_flux"])[0]
+    assert err < 1e-2
