@@ -14,7 +14,11 @@
 // through the face with the smallest exit parameter and the next brick is the
 // one holding the finest cell across that face, so no cell is skipped or
 // visited twice. Bricks at level >= fp64_level compute their entry point and
-// exit parameter in FP64; coarser bricks in FP32.
+// exit parameter in FP64. Coarser bricks compute the entry point in
+// double-float (pairs of FP32 with error-free sums and products), since FP64
+// issues at a small fraction of the FP32 rate on this GPU. Either way the
+// entry point is expressed relative to the entry cell, so FP32 rounding inside
+// a brick scales with the distance marched in it.
 //
 // Accumulation in FP32: N, tau_b and I_b are Kahan-compensated sums;
 // T = exp(-tau) is recomputed from the compensated tau at every cell; the cell
@@ -95,9 +99,12 @@ __device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t xq,
   }
 }
 
-// DDA through a block of nx x ny x nz cells. Q: local entry point (cells),
-// Dl: direction (cells per unit t), tend: block exit relative to entry,
-// (lx, ly, lz): entry cell. Cell (x, y, z) lives at base + z*sz + y*sy + x.
+// DDA through a block of nx x ny x nz cells, entered in cell (lx, ly, lz).
+// Q: entry point relative to the low corner of the entry cell (in cells),
+// Dl: direction (cells per unit t), tend: block exit relative to the entry.
+// Cell (x, y, z) lives at base + z*sz + y*sy + x. Boundary parameters are
+// measured from the entry cell, so their FP32 rounding grows with the distance
+// marched inside the block, not with the ray's distance from the origin.
 // Per-axis state is kept in scalars so the loop stays in registers.
 template <int NBT>
 __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], const float Dl[3],
@@ -111,32 +118,33 @@ __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], c
   const float i0 = Dl[0] != 0.f ? 1.0f / Dl[0] : 0.f;
   const float i1 = Dl[1] != 0.f ? 1.0f / Dl[1] : 0.f;
   const float i2 = Dl[2] != 0.f ? 1.0f / Dl[2] : 0.f;
-  float tm0 = Dl[0] != 0.f ? ((float)(lx + p0) - Q[0]) * i0 : INF;
-  float tm1 = Dl[1] != 0.f ? ((float)(ly + p1) - Q[1]) * i1 : INF;
-  float tm2 = Dl[2] != 0.f ? ((float)(lz + p2) - Q[2]) * i2 : INF;
+  int r0 = 0, r1 = 0, r2 = 0;  // cells stepped from the entry cell
+  float tm0 = Dl[0] != 0.f ? ((float)p0 - Q[0]) * i0 : INF;
+  float tm1 = Dl[1] != 0.f ? ((float)p1 - Q[1]) * i1 : INF;
+  float tm2 = Dl[2] != 0.f ? ((float)p2 - Q[2]) * i2 : INF;
   float tl = 0.f;
   for (;;) {
     const float tn = fminf(fminf(tm0, tm1), fminf(tm2, tend));
     const float ds = tn - tl;
     if (ds > 0.f) {
-      const int64_t idx = base + (int64_t)lz * sz + (int64_t)ly * sy + lx;
+      const int64_t idx = base + (int64_t)(lz + r2) * sz + (int64_t)(ly + r1) * sy + (lx + r0);
       const float rh = __ldg(rho + idx);
       const uint32_t xv = bc.emis ? __ldg(xq + idx) : 0u;
       rt_cell<NBT>(r, rh, xv, ds, bc);
     }
     if (tn >= tend) break;
     if (tm0 <= tm1 && tm0 <= tm2) {
-      lx += s0;
-      if ((unsigned)lx >= (unsigned)nx) break;  // left the block by rounding
-      tm0 = ((float)(lx + p0) - Q[0]) * i0;
+      r0 += s0;
+      if ((unsigned)(lx + r0) >= (unsigned)nx) break;  // left the block
+      tm0 = ((float)(r0 + p0) - Q[0]) * i0;
     } else if (tm1 <= tm2) {
-      ly += s1;
-      if ((unsigned)ly >= (unsigned)ny) break;
-      tm1 = ((float)(ly + p1) - Q[1]) * i1;
+      r1 += s1;
+      if ((unsigned)(ly + r1) >= (unsigned)ny) break;
+      tm1 = ((float)(r1 + p1) - Q[1]) * i1;
     } else {
-      lz += s2;
-      if ((unsigned)lz >= (unsigned)nz) break;
-      tm2 = ((float)(lz + p2) - Q[2]) * i2;
+      r2 += s2;
+      if ((unsigned)(lz + r2) >= (unsigned)nz) break;
+      tm2 = ((float)(r2 + p2) - Q[2]) * i2;
     }
     tl = tn;
   }
@@ -178,38 +186,77 @@ __device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? l
 
 template <int NBT>
 __device__ void march_uniform(RTState<NBT> &r, const GridView &g, const double O[3],
-                              const double D[3], double t0, double t1, const BandCtx &bc) {
+                              const double D[3], double t0, const BandCtx &bc) {
   float Q[3], Dl[3];
   int lc[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const double F = O[a] + t0 * D[a];
     lc[a] = clampi((int)floor(F), 0, g.nf[a] - 1);
-    Q[a] = (float)F;
+    Q[a] = (float)(F - (double)lc[a]);
     Dl[a] = (float)D[a];
   }
-  march_block<NBT>(r, Q, Dl, (float)(t1 - t0), lc[0], lc[1], lc[2], g.nf[0], g.nf[1], g.nf[2], 0,
-                   g.nf[0], (int64_t)g.nf[0] * g.nf[1], g.rho, g.xq, bc);
+  // the ray leaves through a face of the grid: no end parameter needed
+  march_block<NBT>(r, Q, Dl, FLT_MAX, lc[0], lc[1], lc[2], g.nf[0], g.nf[1], g.nf[2], 0, g.nf[0],
+                   (int64_t)g.nf[0] * g.nf[1], g.rho, g.xq, bc);
+}
+
+// Double-float helpers (error-free transformations: Knuth's TwoSum and the
+// fused-multiply-add form of Dekker's TwoProduct).
+struct F2 {
+  float hi, lo;
+};
+__device__ __forceinline__ F2 f2_from(double x) {
+  F2 r;
+  r.hi = (float)x;
+  r.lo = (float)(x - (double)r.hi);
+  return r;
+}
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ F2 f2_add_f(F2 a, float b) {
+  float s, e;
+  two_sum(a.hi, b, s, e);
+  e += a.lo;
+  F2 r;
+  r.hi = s + e;
+  r.lo = e - (r.hi - s);
+  return r;
+}
+// (O + t D - anchor) in finest cells, accurate to FP32 rounding of the result:
+// the products and sums that cancel are carried in double-float.
+__device__ __forceinline__ float f2_offset(F2 O, F2 t, F2 D, float anchor) {
+  const float p = t.hi * D.hi;
+  float pe = fmaf(t.hi, D.hi, -p);            // exact error of t.hi * D.hi
+  pe = fmaf(t.hi, D.lo, fmaf(t.lo, D.hi, pe));
+  float s, se;
+  two_sum(O.hi, p, s, se);
+  const float a = s - anchor;                  // exact: s lies within a cell of anchor
+  return a + ((se + O.lo) + pe);
 }
 
 template <int NBT>
 __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3], const double D[3],
-                          double t0, double t1, int fp64_level, const BandCtx &bc) {
+                          double t0, int fp64_level, const BandCtx &bc) {
   const int B = g.B, lb = g.log2B, Lm = g.Lm;
-  double invD[3];
-  float Of[3], Df[3];
+  F2 Of[3], Df[3];
+  double invD[3], OinvD[3];  // FP64 face parameter: t = face * invD - O * invD
   int c[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
+    Of[a] = f2_from(O[a]);
+    Df[a] = f2_from(D[a]);
     invD[a] = D[a] != 0.0 ? 1.0 / D[a] : 0.0;
-    Of[a] = (float)O[a];
-    Df[a] = (float)D[a];
+    OinvD[a] = O[a] * invD[a];
     c[a] = clampi((int)floor(O[a] + t0 * D[a]), 0, g.nf[a] - 1);
   }
-  double t = t0;
+  F2 t = f2_from(t0);
   const int max_iter = 4 * (g.nf[0] + g.nf[1] + g.nf[2]);
   const int s0 = lb + Lm;
-  for (int it = 0; it < max_iter && t < t1; ++it) {
+  for (int it = 0; it < max_iter; ++it) {
     // leaf brick holding finest cell c
     int code = __ldg(g.base + ((int64_t)(c[2] >> s0) * g.nb0[1] + (c[1] >> s0)) * g.nb0[0] + (c[0] >> s0));
     int lev = 0;
@@ -224,54 +271,61 @@ __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
     const int shift = Lm - bi.w;
     const int S = B << shift;
     const float scale = 1.0f / (float)(1 << shift);
-    float Q[3], Dl[3], tend;
-    double te;
-    int ax = -1;
+    int lc[3], anchor[3];
+    float Q[3], Dl[3], inv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lc[a] = (c[a] - bo[a]) >> shift;
+      anchor[a] = bo[a] + (lc[a] << shift);
+      Dl[a] = Df[a].hi * scale;
+      inv[a] = Dl[a] != 0.f ? 1.0f / Dl[a] : 0.f;
+    }
     const bool deep = bi.w >= fp64_level;
+    // entry point relative to the entry cell, and the exit face: smallest
+    // parameter over the axes, measured from the entry
+    float tend = FLT_MAX;
+    int ax = -1;
+    double te = 0.0;
     if (deep) {
-      te = t1;
+      const double td = (double)t.hi + (double)t.lo;
+      double tmin = DBL_MAX;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
+        Q[a] = (float)(fma(td, D[a], O[a] - (double)anchor[a]) * (double)scale);
         if (D[a] != 0.0) {
           const double face = (double)(D[a] > 0.0 ? bo[a] + S : bo[a]);
-          const double ta = (face - O[a]) * invD[a];
-          if (ta < te) {
-            te = ta;
+          const double ta = fma(face, invD[a], -OinvD[a]);
+          if (ta < tmin) {
+            tmin = ta;
             ax = a;
           }
         }
-        Q[a] = (float)fma(t, D[a], O[a] - (double)bo[a]) * scale;
-        Dl[a] = Df[a] * scale;
       }
-      if (te < t) te = t;
-      tend = (float)(te - t);
+      te = tmin < td ? td : tmin;
+      tend = (float)(te - td);
     } else {
-      const float tf = (float)t;
-      float tr = (float)(t1 - t);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        Q[a] = (fmaf(tf, Df[a], Of[a]) - (float)bo[a]) * scale;
-        Dl[a] = Df[a] * scale;
-        if (Df[a] != 0.f) {
-          const float ta = ((Df[a] > 0.f ? (float)B : 0.f) - Q[a]) / Dl[a];
-          if (ta < tr) {
-            tr = ta;
+        Q[a] = f2_offset(Of[a], t, Df[a], (float)anchor[a]) * scale;
+        if (Dl[a] != 0.f) {
+          const float face = Dl[a] > 0.f ? (float)(B - lc[a]) : (float)(-lc[a]);
+          const float ta = (face - Q[a]) * inv[a];
+          if (ta < tend) {
+            tend = ta;
             ax = a;
           }
         }
       }
-      if (tr < 0.f) tr = 0.f;
-      tend = tr;
-      te = ax < 0 ? t1 : t + (double)tr;
+      if (tend < 0.f) tend = 0.f;
     }
-    int lc[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) lc[a] = (c[a] - bo[a]) >> shift;
     march_block<NBT>(r, Q, Dl, tend, lc[0], lc[1], lc[2], B, B, B, (int64_t)code << (3 * lb), B,
                      (int64_t)B * B, g.rho, g.xq, bc);
     if (ax < 0) break;
-    t = te;
-    // finest cell just across the exit face; the other coordinates stay in this brick's range
+    // advance to the exit point
+    if (deep) t = f2_from(te);
+    else t = f2_add_f(t, tend);
+    // finest cell just across the exit face; the other coordinates, from the
+    // exit point in this brick's frame, stay in this brick's range
     bool out = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -279,8 +333,9 @@ __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
         c[a] = D[a] > 0.0 ? bo[a] + S : bo[a] - 1;
         out = c[a] < 0 || c[a] >= g.nf[a];
       } else {
-        const double F = deep ? fma(te, D[a], O[a]) : (double)fmaf((float)te, Df[a], Of[a]);
-        c[a] = clampi((int)floor(F), bo[a], bo[a] + S - 1);
+        const float e = fmaf(tend, Dl[a], Q[a]);  // local cells from the entry cell
+        const int f = anchor[a] + (int)floorf(e * (float)(1 << shift));
+        c[a] = clampi(f, bo[a], bo[a] + S - 1);
       }
     }
     if (out) break;
@@ -344,9 +399,9 @@ __global__ void __launch_bounds__(256) k_march(GridView g, Camera cam, RaySource
   double O[3], D[3], t0, t1;
   if (ray_setup(g, cam, n0, L, i, j, O, D, t0, t1)) {
     if (AMR)
-      march_amr<NBT>(st, g, O, D, t0, t1, fp64_level, bc);
+      march_amr<NBT>(st, g, O, D, t0, fp64_level, bc);
     else
-      march_uniform<NBT>(st, g, O, D, t0, t1, bc);
+      march_uniform<NBT>(st, g, O, D, t0, bc);
   }
   if (chunk == 0) {
     out.N[k] = st.N;
