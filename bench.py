@@ -159,10 +159,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="one adaptive image of the workload after --warmup images, then exit "
+                         "(the case profiled with ncu)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    assert args.warmup >= 3, "at least 3 warm-up steps"
+    assert args.warmup >= 3 or args.profile_case, "at least 3 warm-up steps"
 
     import torch
     import torch.distributed as dist
@@ -192,6 +195,13 @@ def main():
         return g.render_adaptive(view, W["base_res"], W["max_level"], W["xi_crit"], mem=mem,
                                  capacity=cap)
 
+    if args.profile_case:
+        for _ in range(args.warmup + 1):
+            r = render()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "air", "rays": r["n_rays"], "steps": r["n_steps"],
+                          "sweeps": r["n_sweeps"]}), flush=True)
+        return
     r = render()
     cap = r["n_out"]
     for _ in range(args.warmup):
