@@ -161,6 +161,32 @@ AIR_API air_status air_profile_enable(air_grid *g, int32_t on);
  * phase p < AIR_N_PHASES (either pointer may be NULL). */
 AIR_API air_status air_profile_read(air_grid *g, double *ms, int64_t *launches);
 
+/* Band flux of an image already in device memory, computed without allocating
+ * any memory. The paper has no counterpart: this is a service for callers that
+ * cannot call cudaMalloc when they need the flux -- a real-time or serving loop
+ * that must not stall the device (cudaFree synchronises it), a plugin whose
+ * host application owns all device memory through its own pool, or code that
+ * runs where the CUDA runtime forbids allocation.
+ *   band_flux[b] = sum over entries k < n with is_leaf[k] != 0 (every entry if
+ *   is_leaf is NULL) of intensity[b * stride + k] * area0 / 4^level[k]
+ *   (level 0 if level is NULL); area0 is the pixel area at level 0, e.g.
+ *   (2H / base_res)^2. The result matches the band_flux of the render that
+ *   produced the arrays up to FP64 summation order.
+ * All arrays are device memory (checked); the work is queued on `stream` (a
+ * cudaStream_t, NULL = legacy default stream) and band_flux is valid once the
+ * stream reaches that point; the call does not synchronise.
+ * Scratch: a fixed 512 KiB device array inside this library (1024 partial sums
+ * x 64 bands), which every GPU that loads the library holds until the process
+ * exits. Limits: 1 <= n_bands <= 64 and 0 <= n <= 2^31 - 1; larger requests
+ * fail with AIR_ERR_ARG. The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture. Every call shares the array and
+ * overwrites the partial sums it uses, so nothing needs clearing, but calls
+ * whose work overlaps on the GPU (other streams, other threads) race on it. */
+AIR_API air_status air_band_flux_static(const float *intensity, int64_t stride, int32_t n_bands,
+                                        const int32_t *level, const uint8_t *is_leaf, int64_t n,
+                                        double area0, double *band_flux, void *stream);
+
 /* Release the device copy and every buffer the handle holds. NULL is a no-op. */
 AIR_API void air_free(air_grid *g);
 

@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_HERE, "libair_gb300.so")
-SOURCES = ["air_api.cu", "air_grid.cu", "air_march.cu", "air_refine.cu"]
+SOURCES = ["air_api.cu", "air_grid.cu", "air_march.cu", "air_refine.cu", "air_static.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 
@@ -31,7 +31,8 @@ AIR_OK, AIR_ERR_ARG, AIR_ERR_OOM, AIR_ERR_CUDA, AIR_ERR_CAPACITY, AIR_ERR_TIMEOU
 AIR_HOST, AIR_DEVICE = 0, 1
 
 EXPORTED = ["air_load_grid", "air_set_stream", "air_render_fixed", "air_render_adaptive",
-            "air_profile_enable", "air_profile_read", "air_free", "air_last_error", "air_version"]
+            "air_profile_enable", "air_profile_read", "air_band_flux_static", "air_free",
+            "air_last_error", "air_version"]
 PHASES = ("march", "scan", "balance", "refine", "output")
 
 
@@ -133,6 +134,10 @@ def lib():
             L.air_profile_enable.argtypes = [C.c_void_p, C.c_int32]
             L.air_profile_read.restype = C.c_int
             L.air_profile_read.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+            L.air_band_flux_static.restype = C.c_int
+            L.air_band_flux_static.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
+                                               C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
+                                               C.c_void_p]
             L.air_free.restype = None
             L.air_free.argtypes = [C.c_void_p]
             L.air_last_error.restype = C.c_char_p
@@ -293,6 +298,24 @@ class Grid:
         _check(st)
         self._cap_hint = max(self._cap_hint, int(im.n_out))
         return self._result(im, out)
+
+
+def band_flux_static(intensity, n, area0, level=None, is_leaf=None, out=None):
+    """air_band_flux_static: band flux of a device image with no allocation in
+    the library. `intensity` is a [n_bands, stride] CUDA tensor (row stride
+    `stride`), `level` / `is_leaf` optional CUDA tensors, `out` a float64 CUDA
+    tensor of n_bands entries (allocated here if None, by the caller's torch)."""
+    import torch
+    nb = intensity.shape[0]
+    if out is None:
+        out = torch.empty(nb, dtype=torch.float64, device=intensity.device)
+    st = lib().air_band_flux_static(
+        C.c_void_p(intensity.data_ptr()), int(intensity.stride(0)), int(nb),
+        C.c_void_p(level.data_ptr()) if level is not None else None,
+        C.c_void_p(is_leaf.data_ptr()) if is_leaf is not None else None, int(n), float(area0),
+        C.c_void_p(out.data_ptr()), _stream())
+    _check(st)
+    return out
 
 
 def version() -> str:
