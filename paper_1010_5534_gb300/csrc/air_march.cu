@@ -39,9 +39,14 @@ struct RTState {
 
 struct BandCtx {
   const float *tab;  // shared: [NBT][tstride]
-  const float *kap;  // shared: [NBT]
-  const float *ik;   // shared: [NBT]
   int tstride, nbh, emis;
+};
+
+// Per-band constants held in registers for the whole ray.
+template <int NBT>
+struct BandRegs {
+  float kap[NBT];  // kappa_b
+  float ik[NBT];   // 1 / kappa_b (0 where kappa_b = 0)
 };
 
 template <int NBT>
@@ -62,7 +67,7 @@ __device__ __forceinline__ void rt_init(RTState<NBT> &r) {
 // One cell chord of length ds with density rho and table coordinate xq.
 template <int NBT>
 __device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t xq, float ds,
-                                        const BandCtx &bc) {
+                                        const BandCtx &bc, const BandRegs<NBT> &br) {
   kahan_add(r.N, r.cN, rho * ds);
   r.steps += 1;
   int k = 0;
@@ -80,7 +85,7 @@ __device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t xq,
         const float *t = bc.tab + b * bc.tstride + k;
         lam = fmaf(w, t[1] - t[0], t[0]);
       }
-      const float alpha = bc.kap[b] * rho;
+      const float alpha = br.kap[b] * rho;
       const float dtau = alpha * ds;
       float term;
       if (dtau > 0.f) {
@@ -89,7 +94,7 @@ __device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t xq,
         if (dtau < 0.25f)
           term = rho2ds * lam * r.T[b] * one_minus_exp_over_x(dtau);
         else
-          term = rho * lam * bc.ik[b] * (r.T[b] - Tn);
+          term = rho * lam * br.ik[b] * (r.T[b] - Tn);
         r.T[b] = Tn;
       } else {
         term = rho2ds * lam * r.T[b];
@@ -102,74 +107,99 @@ __device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t xq,
 // DDA through a block of nx x ny x nz cells, entered in cell (lx, ly, lz).
 // Q: entry point relative to the low corner of the entry cell (in cells),
 // Dl: direction (cells per unit t), tend: block exit relative to the entry.
-// Cell (x, y, z) lives at base + z*sz + y*sy + x. Boundary parameters are
-// measured from the entry cell, so their FP32 rounding grows with the distance
-// marched inside the block, not with the ray's distance from the origin.
-// Per-axis state is kept in scalars so the loop stays in registers.
-template <int NBT>
+// rho / xq point at the block's cell (0, 0, 0); cell (x, y, z) is at
+// z*sz + y*sy + x. Boundary parameters are measured from the entry cell, so
+// their FP32 rounding grows with the distance marched inside the block, not
+// with the ray's distance from the origin. The fields of the next cell are
+// fetched before the current cell's transfer step, so the load latency
+// overlaps that arithmetic. Per-axis state is kept in scalars (registers).
+template <int NBT, typename Idx>
 __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], const float Dl[3],
                                             float tend, int lx, int ly, int lz, int nx, int ny,
-                                            int nz, int64_t base, int64_t sy, int64_t sz,
-                                            const float *__restrict__ rho,
-                                            const uint32_t *__restrict__ xq, const BandCtx &bc) {
+                                            int nz, Idx sy, Idx sz, const float *__restrict__ rho,
+                                            const uint32_t *__restrict__ xq, const BandCtx &bc,
+                                            const BandRegs<NBT> &br) {
   const float INF = FLT_MAX;
   const int s0 = Dl[0] > 0.f ? 1 : -1, s1 = Dl[1] > 0.f ? 1 : -1, s2 = Dl[2] > 0.f ? 1 : -1;
   const int p0 = Dl[0] > 0.f, p1 = Dl[1] > 0.f, p2 = Dl[2] > 0.f;
   const float i0 = Dl[0] != 0.f ? 1.0f / Dl[0] : 0.f;
   const float i1 = Dl[1] != 0.f ? 1.0f / Dl[1] : 0.f;
   const float i2 = Dl[2] != 0.f ? 1.0f / Dl[2] : 0.f;
+  const Idx d0 = (Idx)s0, d1 = (Idx)s1 * sy, d2 = (Idx)s2 * sz;
   int r0 = 0, r1 = 0, r2 = 0;  // cells stepped from the entry cell
   float tm0 = Dl[0] != 0.f ? ((float)p0 - Q[0]) * i0 : INF;
   float tm1 = Dl[1] != 0.f ? ((float)p1 - Q[1]) * i1 : INF;
   float tm2 = Dl[2] != 0.f ? ((float)p2 - Q[2]) * i2 : INF;
+  Idx idx = (Idx)lz * sz + (Idx)ly * sy + (Idx)lx;
+  float rh = __ldg(rho + idx);
+  uint32_t xv = bc.emis ? __ldg(xq + idx) : 0u;
   float tl = 0.f;
   for (;;) {
     const float tn = fminf(fminf(tm0, tm1), fminf(tm2, tend));
     const float ds = tn - tl;
-    if (ds > 0.f) {
-      const int64_t idx = base + (int64_t)(lz + r2) * sz + (int64_t)(ly + r1) * sy + (lx + r0);
-      const float rh = __ldg(rho + idx);
-      const uint32_t xv = bc.emis ? __ldg(xq + idx) : 0u;
-      rt_cell<NBT>(r, rh, xv, ds, bc);
+    bool more = tn < tend;
+    float rh_n = 0.f;
+    uint32_t xv_n = 0u;
+    if (more) {
+      if (tm0 <= tm1 && tm0 <= tm2) {
+        r0 += s0;
+        more = (unsigned)(lx + r0) < (unsigned)nx;
+        idx += d0;
+        tm0 = ((float)(r0 + p0) - Q[0]) * i0;
+      } else if (tm1 <= tm2) {
+        r1 += s1;
+        more = (unsigned)(ly + r1) < (unsigned)ny;
+        idx += d1;
+        tm1 = ((float)(r1 + p1) - Q[1]) * i1;
+      } else {
+        r2 += s2;
+        more = (unsigned)(lz + r2) < (unsigned)nz;
+        idx += d2;
+        tm2 = ((float)(r2 + p2) - Q[2]) * i2;
+      }
+      if (more) {
+        rh_n = __ldg(rho + idx);
+        if (bc.emis) xv_n = __ldg(xq + idx);
+      }
     }
-    if (tn >= tend) break;
-    if (tm0 <= tm1 && tm0 <= tm2) {
-      r0 += s0;
-      if ((unsigned)(lx + r0) >= (unsigned)nx) break;  // left the block
-      tm0 = ((float)(r0 + p0) - Q[0]) * i0;
-    } else if (tm1 <= tm2) {
-      r1 += s1;
-      if ((unsigned)(ly + r1) >= (unsigned)ny) break;
-      tm1 = ((float)(r1 + p1) - Q[1]) * i1;
-    } else {
-      r2 += s2;
-      if ((unsigned)(lz + r2) >= (unsigned)nz) break;
-      tm2 = ((float)(r2 + p2) - Q[2]) * i2;
-    }
+    if (ds > 0.f) rt_cell<NBT>(r, rh, xv, ds, bc, br);
+    if (!more) break;  // left the block (through its far face, or by rounding)
+    rh = rh_n;
+    xv = xv_n;
     tl = tn;
   }
 }
 
-// Pixel centre -> ray in finest-cell units, clipped to the box: F(t) = O + t D.
-__device__ __forceinline__ bool ray_setup(const GridView &g, const Camera &cam, int n0, int L,
-                                          int i, int j, double O[3], double D[3], double &t0,
-                                          double &t1) {
-  const double nL = (double)n0 * (double)(1u << L);
-  const double pix = (2.0 * cam.H) / nL;
-  const double uc = -cam.H + ((double)i + 0.5) * pix;
-  const double vc = -cam.H + ((double)j + 0.5) * pix;
+// Per-launch ray geometry, resolved on the host in FP64 in finest-cell units:
+// the pixel centre (uc, vc) maps to O = A + uc U + vc V, rays travel along D.
+struct RayGeom {
+  double A[3], U[3], V[3], D[3], invD[3];
+  double H, pix0;  // image half-extent, pixel size at level 0
+};
+
+// 2^-L exactly (0 <= L < 1023).
+__device__ __forceinline__ double exp2_neg(int L) {
+  return __longlong_as_double((long long)(1023 - L) << 52);
+}
+
+// Pixel centre -> ray in finest-cell units, clipped to the box: F(t) = O + t D,
+// t >= t0. The pixel size at level L is pix0 2^-L (exact scaling), so a pixel
+// of an adaptive image and the same pixel of a fixed image get the same ray.
+__device__ __forceinline__ bool ray_setup(const GridView &g, const RayGeom &rg, int L, int i,
+                                          int j, double O[3], double &t0) {
+  const double pix = rg.pix0 * exp2_neg(L);
+  const double uc = fma((double)i + 0.5, pix, -rg.H);
+  const double vc = fma((double)j + 0.5, pix, -rg.H);
   t0 = -DBL_MAX;
-  t1 = DBL_MAX;
+  double t1 = DBL_MAX;
   bool hit = true;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double o = cam.c[a] + uc * cam.u[a] + vc * cam.v[a];
-    O[a] = (o - g.lo[a]) / g.h[a];
-    D[a] = cam.d[a] / g.h[a];
-    if (cam.d[a] == 0.0) {
+    O[a] = fma(vc, rg.V[a], fma(uc, rg.U[a], rg.A[a]));
+    if (rg.D[a] == 0.0) {
       if (!(O[a] >= 0.0 && O[a] < (double)g.nf[a])) hit = false;
     } else {
-      double ta = (0.0 - O[a]) / D[a], tb = ((double)g.nf[a] - O[a]) / D[a];
+      double ta = -O[a] * rg.invD[a], tb = ((double)g.nf[a] - O[a]) * rg.invD[a];
       if (ta > tb) {
         const double x = ta;
         ta = tb;
@@ -186,7 +216,8 @@ __device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? l
 
 template <int NBT>
 __device__ void march_uniform(RTState<NBT> &r, const GridView &g, const double O[3],
-                              const double D[3], double t0, const BandCtx &bc) {
+                              const double D[3], double t0, const BandCtx &bc,
+                              const BandRegs<NBT> &br) {
   float Q[3], Dl[3];
   int lc[3];
 #pragma unroll
@@ -197,8 +228,8 @@ __device__ void march_uniform(RTState<NBT> &r, const GridView &g, const double O
     Dl[a] = (float)D[a];
   }
   // the ray leaves through a face of the grid: no end parameter needed
-  march_block<NBT>(r, Q, Dl, FLT_MAX, lc[0], lc[1], lc[2], g.nf[0], g.nf[1], g.nf[2], 0, g.nf[0],
-                   (int64_t)g.nf[0] * g.nf[1], g.rho, g.xq, bc);
+  march_block<NBT, int64_t>(r, Q, Dl, FLT_MAX, lc[0], lc[1], lc[2], g.nf[0], g.nf[1], g.nf[2],
+                            (int64_t)g.nf[0], (int64_t)g.nf[0] * g.nf[1], g.rho, g.xq, bc, br);
 }
 
 // Double-float helpers (error-free transformations: Knuth's TwoSum and the
@@ -240,16 +271,16 @@ __device__ __forceinline__ float f2_offset(F2 O, F2 t, F2 D, float anchor) {
 
 template <int NBT>
 __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3], const double D[3],
-                          double t0, int fp64_level, const BandCtx &bc) {
+                          const double invD[3], double t0, int fp64_level, const BandCtx &bc,
+                          const BandRegs<NBT> &br) {
   const int B = g.B, lb = g.log2B, Lm = g.Lm;
   F2 Of[3], Df[3];
-  double invD[3], OinvD[3];  // FP64 face parameter: t = face * invD - O * invD
+  double OinvD[3];  // FP64 face parameter: t = face * invD - O * invD
   int c[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     Of[a] = f2_from(O[a]);
     Df[a] = f2_from(D[a]);
-    invD[a] = D[a] != 0.0 ? 1.0 / D[a] : 0.0;
     OinvD[a] = O[a] * invD[a];
     c[a] = clampi((int)floor(O[a] + t0 * D[a]), 0, g.nf[a] - 1);
   }
@@ -318,8 +349,9 @@ __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
       }
       if (tend < 0.f) tend = 0.f;
     }
-    march_block<NBT>(r, Q, Dl, tend, lc[0], lc[1], lc[2], B, B, B, (int64_t)code << (3 * lb), B,
-                     (int64_t)B * B, g.rho, g.xq, bc);
+    const int64_t boff = (int64_t)code << (3 * lb);
+    march_block<NBT, int>(r, Q, Dl, tend, lc[0], lc[1], lc[2], B, B, B, B, B * B, g.rho + boff,
+                          g.xq ? g.xq + boff : nullptr, bc, br);
     if (ax < 0) break;
     // advance to the exit point
     if (deep) t = f2_from(te);
@@ -342,9 +374,16 @@ __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
   }
 }
 
+template <int NBT>
+struct MinBlocks {
+  static constexpr int value = NBT <= 1 ? 6 : (NBT <= 2 ? 5 : (NBT <= 4 ? 4 : (NBT <= 8 ? 3 : 2)));
+};
+
+constexpr int kMarchBlock = 128;
+
 template <int NBT, bool AMR>
-__global__ void __launch_bounds__(256) k_march(GridView g, Camera cam, RaySource src, RayOut out,
-                                               int fp64_level) {
+__global__ void __launch_bounds__(kMarchBlock, MinBlocks<NBT>::value)
+    k_march(GridView g, RayGeom rg, RaySource src, RayOut out, int fp64_level) {
   extern __shared__ float smem[];
   const int chunk = blockIdx.y;
   const int b0 = chunk * NBT;
@@ -352,25 +391,21 @@ __global__ void __launch_bounds__(256) k_march(GridView g, Camera cam, RaySource
   const int tstride = g.n_tbins + 1;
   BandCtx bc;
   bc.tab = smem;
-  bc.kap = smem + NBT * tstride;
-  bc.ik = bc.kap + NBT;
   bc.tstride = tstride;
   bc.nbh = nbh;
   bc.emis = g.emis_mode;
-  {
-    float *tab = smem;
-    if (g.emis_mode)
-      for (int x = threadIdx.x; x < nbh * tstride; x += blockDim.x) tab[x] = g.table[b0 * tstride + x];
-    float *kap = smem + NBT * tstride;
-    for (int x = threadIdx.x; x < NBT; x += blockDim.x) {
-      kap[x] = x < nbh ? g.kappa[b0 + x] : 0.f;
-      kap[NBT + x] = x < nbh ? g.invkappa[b0 + x] : 0.f;
-    }
+  if (g.emis_mode)
+    for (int x = threadIdx.x; x < nbh * tstride; x += blockDim.x) smem[x] = g.table[b0 * tstride + x];
+  BandRegs<NBT> br;
+#pragma unroll
+  for (int b = 0; b < NBT; ++b) {
+    br.kap[b] = b < nbh ? __ldg(g.kappa + b0 + b) : 0.f;
+    br.ik[b] = b < nbh ? __ldg(g.invkappa + b0 + b) : 0.f;
   }
   __syncthreads();
 
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int L, i, j, n0;
+  int L, i, j;
   int64_t k;
   if (src.mode == 0) {
     if (r >= src.count) return;
@@ -378,7 +413,6 @@ __global__ void __launch_bounds__(256) k_march(GridView g, Camera cam, RaySource
     L = src.lvl[k];
     i = src.pi[k];
     j = src.pj[k];
-    n0 = src.n0;
   } else {
     const int res = src.n0;
     const int tw = src.tile_w, th = 32 / tw;
@@ -392,16 +426,15 @@ __global__ void __launch_bounds__(256) k_march(GridView g, Camera cam, RaySource
     if (i >= res || j >= res) return;
     k = (int64_t)j * res + i;
     L = 0;
-    n0 = res;
   }
   RTState<NBT> st;
   rt_init<NBT>(st);
-  double O[3], D[3], t0, t1;
-  if (ray_setup(g, cam, n0, L, i, j, O, D, t0, t1)) {
+  double O[3], t0;
+  if (ray_setup(g, rg, L, i, j, O, t0)) {
     if (AMR)
-      march_amr<NBT>(st, g, O, D, t0, fp64_level, bc);
+      march_amr<NBT>(st, g, O, rg.D, rg.invD, t0, fp64_level, bc, br);
     else
-      march_uniform<NBT>(st, g, O, D, t0, bc);
+      march_uniform<NBT>(st, g, O, rg.D, t0, bc, br);
   }
   if (chunk == 0) {
     out.N[k] = st.N;
@@ -429,6 +462,21 @@ __global__ void k_band_sum(const float *__restrict__ I, int n_bands, int64_t str
   p[k] = s;
 }
 
+// World camera -> per-launch ray geometry in finest-cell units (FP64, host).
+static RayGeom make_geom(const GridView &g, const Camera &cam, int n0) {
+  RayGeom rg;
+  for (int a = 0; a < 3; ++a) {
+    rg.A[a] = (cam.c[a] - g.lo[a]) / g.h[a];
+    rg.U[a] = cam.u[a] / g.h[a];
+    rg.V[a] = cam.v[a] / g.h[a];
+    rg.D[a] = cam.d[a] / g.h[a];
+    rg.invD[a] = cam.d[a] != 0.0 ? 1.0 / rg.D[a] : 0.0;
+  }
+  rg.H = cam.H;
+  rg.pix0 = (2.0 * cam.H) / (double)n0;
+  return rg;
+}
+
 template <int NBT>
 static cudaError_t launch_t(const GridView &g, const Camera &cam, const RaySource &src,
                             const RayOut &out, const MarchTune &tune, cudaStream_t st) {
@@ -442,15 +490,16 @@ static cudaError_t launch_t(const GridView &g, const Camera &cam, const RaySourc
     threads = tiles * 32;
   }
   if (threads <= 0) return cudaSuccess;
-  const int block = tune.block;
+  const int block = kMarchBlock;
   const int64_t blocks = (threads + block - 1) / block;
   if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(float) * (size_t)(NBT * (g.n_tbins + 1) + 2 * NBT);
+  const size_t smem = sizeof(float) * (size_t)(NBT * (g.n_tbins + 1));
+  const RayGeom rg = make_geom(g, cam, src.n0);
   dim3 grid((unsigned)blocks, chunks);
   if (g.kind == AIR_GRID_AMR)
-    k_march<NBT, true><<<grid, block, smem, st>>>(g, cam, src, out, tune.fp64_level);
+    k_march<NBT, true><<<grid, block, smem, st>>>(g, rg, src, out, tune.fp64_level);
   else
-    k_march<NBT, false><<<grid, block, smem, st>>>(g, cam, src, out, tune.fp64_level);
+    k_march<NBT, false><<<grid, block, smem, st>>>(g, rg, src, out, tune.fp64_level);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (chunks > 1 && out.p) {
