@@ -169,12 +169,34 @@ def _cone_distance(px, py, pz, apex, half_angle):
     return d, on_sheet
 
 
+def _lattice_noise(lattice, lo, scale, PX, PY, PZ):
+    """Unit-variance field: trilinear interpolation of lattice normals, divided
+    pointwise by the root of the summed squared weights."""
+    n = lattice.shape[0]
+    acc = np.zeros(PX.shape)
+    w2 = np.zeros(PX.shape)
+    g = [(P - lo) / scale for P in (PX, PY, PZ)]
+    i = [np.clip(np.floor(x).astype(np.int64), 0, n - 2) for x in g]
+    f = [x - k for x, k in zip(g, i)]
+    for dz in (0, 1):
+        wz = f[2] if dz else 1.0 - f[2]
+        for dy in (0, 1):
+            wy = f[1] if dy else 1.0 - f[1]
+            for dx in (0, 1):
+                wx = f[0] if dx else 1.0 - f[0]
+                w = wx * wy * wz
+                acc += w * lattice[i[2] + dz, i[1] + dy, i[0] + dx]
+                w2 += w * w
+    return acc / np.sqrt(w2)
+
+
 def cone_shock_amr(seed: int = 0, n_base: int = 128, brick: int = 16, levels: int = 3,
                    n_bands: int = 1, e_lo: float = 1.0, e_hi: float = 10.0,
                    kappa0: float = 0.3, half_angle_deg: float = 30.0,
                    thickness: float = 0.04, apex=(-0.5, 0.0, 0.0),
                    star=(-0.8, 0.0, 0.0), clump_sigma: float = 0.3,
-                   n_tbins: int = 64, refine_margin: float = 1.0) -> Scene:
+                   clump_scale: float = 0.0, n_tbins: int = 64,
+                   refine_margin: float = 1.0) -> Scene:
     """Block-AMR grid over [-1,1]^3: n_base^3 base cells in brick^3 bricks,
     `levels` refinement levels (factor 2) on bricks near a conical shock
     (apex `apex`, axis +x, half-angle 30 deg, shell thickness 0.04 = 0.02 of the
@@ -183,7 +205,12 @@ def cone_shock_amr(seed: int = 0, n_base: int = 128, brick: int = 16, levels: in
 
     Fields (FP32, sampled at cell centres of each leaf brick at its own level):
       rho = rho_w * (4 in the shocked shell, 0.25 inside the cone, 1 outside)
-            * exp(0.3 z - 0.045), z ~ N(0,1) per cell (lognormal clumping)
+            * exp(0.3 z - 0.045)  (lognormal clumping, z ~ N(0,1))
+      z is drawn independently per cell (clump_scale = 0, the default), or is a
+      clump field of correlation length clump_scale > 0: unit normals on a
+      lattice of that spacing, trilinearly interpolated and renormalised to
+      unit variance at every point, so z is a function of position, the same in
+      coarse and fine bricks.
       rho_w = max(|x - star|, 0.05)^-2
       T = 10^7.5 K in the shell, 10^4 K elsewhere.
     Emission: j_b = rho^2 Lambda_b(T) (64-bin table), absorption kappa_b rho with
@@ -227,35 +254,42 @@ def cone_shock_amr(seed: int = 0, n_base: int = 128, brick: int = 16, levels: in
     origins = np.concatenate(leaf_origins, axis=0)
     nb = len(levels_arr)
 
-    # fields at cell centres, brick by brick (vectorised per level)
+    # fields at cell centres, brick by brick (vectorised over chunks of bricks)
     rho = np.empty((nb, brick, brick, brick), dtype=np.float32)
     temp = np.empty((nb, brick, brick, brick), dtype=np.float32)
     off = np.arange(brick) + 0.5
-    start = 0
-    noise = rng.standard_normal(nb * brick ** 3).reshape(nb, brick, brick, brick)
+    if clump_scale > 0:
+        nl = int(math.ceil((hi - lo) / clump_scale)) + 2
+        lattice = rng.standard_normal((nl, nl, nl))
+    else:
+        cell_noise = rng.standard_normal(nb * brick ** 3).reshape(nb, brick, brick, brick)
+    chunk = max(1, (1 << 22) // brick ** 3)
     for lev in range(levels + 1):
-        sel = np.nonzero(levels_arr == lev)[0]
-        if len(sel) == 0:
-            continue
+        sel_all = np.nonzero(levels_arr == lev)[0]
         step = 1 << (levels - lev)
-        o = origins[sel].astype(np.float64)
-        # [nsel, B] coordinates per axis
-        cx = lo + (o[:, 0:1] + off[None, :] * step) * hf
-        cy = lo + (o[:, 1:2] + off[None, :] * step) * hf
-        cz = lo + (o[:, 2:3] + off[None, :] * step) * hf
-        PX = np.broadcast_to(cx[:, None, None, :], (len(sel), brick, brick, brick))
-        PY = np.broadcast_to(cy[:, None, :, None], (len(sel), brick, brick, brick))
-        PZ = np.broadcast_to(cz[:, :, None, None], (len(sel), brick, brick, brick))
-        rw = np.sqrt((PX - star[0]) ** 2 + (PY - star[1]) ** 2 + (PZ - star[2]) ** 2)
-        rho_w = np.maximum(rw, 0.05) ** -2
-        d, on_sheet = _cone_distance(PX, PY, PZ, apex, half_angle)
-        shell = (np.abs(d) <= thickness / 2) & on_sheet
-        inside = (d < -thickness / 2) & on_sheet
-        fac = np.where(shell, 4.0, np.where(inside, 0.25, 1.0))
-        clump = np.exp(clump_sigma * noise[sel] - 0.5 * clump_sigma ** 2)
-        rho[sel] = (rho_w * fac * clump).astype(np.float32)
-        temp[sel] = np.where(shell, 10.0 ** 7.5, 1e4).astype(np.float32)
-        start += len(sel)
+        for c0 in range(0, len(sel_all), chunk):
+            sel = sel_all[c0:c0 + chunk]
+            o = origins[sel].astype(np.float64)
+            cx = lo + (o[:, 0:1] + off[None, :] * step) * hf
+            cy = lo + (o[:, 1:2] + off[None, :] * step) * hf
+            cz = lo + (o[:, 2:3] + off[None, :] * step) * hf
+            shp = (len(sel), brick, brick, brick)
+            PX = np.broadcast_to(cx[:, None, None, :], shp)
+            PY = np.broadcast_to(cy[:, None, :, None], shp)
+            PZ = np.broadcast_to(cz[:, :, None, None], shp)
+            rw = np.sqrt((PX - star[0]) ** 2 + (PY - star[1]) ** 2 + (PZ - star[2]) ** 2)
+            rho_w = np.maximum(rw, 0.05) ** -2
+            d, on_sheet = _cone_distance(PX, PY, PZ, apex, half_angle)
+            shell = (np.abs(d) <= thickness / 2) & on_sheet
+            inside = (d < -thickness / 2) & on_sheet
+            fac = np.where(shell, 4.0, np.where(inside, 0.25, 1.0))
+            if clump_scale > 0:
+                z = _lattice_noise(lattice, lo, clump_scale, PX, PY, PZ)
+            else:
+                z = cell_noise[sel]
+            clump = np.exp(clump_sigma * z - 0.5 * clump_sigma ** 2)
+            rho[sel] = (rho_w * fac * clump).astype(np.float32)
+            temp[sel] = np.where(shell, 10.0 ** 7.5, 1e4).astype(np.float32)
 
     edges = band_edges(n_bands, e_lo, e_hi)
     return Scene(kind="amr", lo=(lo,) * 3, hi=(hi,) * 3, n=(n_base,) * 3, rho=rho, temp=temp,
@@ -263,7 +297,7 @@ def cone_shock_amr(seed: int = 0, n_base: int = 128, brick: int = 16, levels: in
                  brick_origin=origins.astype(np.int32), emis_mode=1,
                  lambda_table=cooling_table(edges, n_tbins), logT_lo=4.0, logT_hi=9.0,
                  kappa=band_kappa(edges, kappa0),
-                 name=f"cone_amr_{n_base}^3_b{brick}_L{levels}_{n_bands}band_s{seed}")
+                 name=f"cone_amr_{n_base}^3_b{brick}_L{levels}_{n_bands}band_c{clump_scale}_s{seed}")
 
 
 # --------------------------------------------------------------------------
