@@ -145,6 +145,35 @@ AIR_API air_status air_render_fixed(air_grid *g, const air_view *view, int32_t r
 AIR_API air_status air_render_adaptive(air_grid *g, const air_view *view, const air_params *params,
                                air_image *out);
 
+/* Options of a batched render. Zero-initialise and set what you need, or pass
+ * NULL for the defaults. */
+typedef struct {
+  int32_t bands_per_thread;   /* bands one thread carries along a ray: 1, 2, 4, 8 or 16;
+                                 0 = library default (8 for more than 4 bands) */
+  int32_t use_graph;          /* 1: launch through a CUDA graph captured on first use
+                                 (re-captured when the configuration changes) */
+  double wait_timeout_ms;     /* time limit of every device-side wait of the persistent
+                                 kernel (grid barriers); <= 0 means 2000 ms. A wait that
+                                 runs out makes the call return AIR_ERR_TIMEOUT. */
+  int32_t test_stall_barrier; /* fault test: the first grid barrier waits for one block
+                                 more than is launched, so it must run out (0 in use) */
+} air_batch_opts;
+
+/* Batched adaptive images (Section 2 steps i-vi for every view): n_views views
+ * of one grid, each with all the grid's bands, each refined on its own image,
+ * rendered by one cooperative persistent kernel that runs every sweep of every
+ * view (a work queue of (ray, band chunk) items for the march; scan, balance
+ * and a per-view prefix sum between grid barriers), launched through a CUDA
+ * graph. outs[v] receives view v exactly as air_render_adaptive would (same
+ * pixels, same order); band fluxes are summed with FP64 atomics (equal to the
+ * single-view result up to FP64 summation order). The views share params
+ * (and the image half-extent used for pixel areas is per view). At most 256
+ * views; every view's node list shares the handle's workspace, grown (and the
+ * render repeated) when a batch does not fit. */
+AIR_API air_status air_render_batch(air_grid *g, const air_view *views, int32_t n_views,
+                                    const air_params *params, const air_batch_opts *opts,
+                                    air_image *outs);
+
 /* Phase profiling: when enabled, every kernel launch group of a render is
  * bracketed by CUDA events on the handle's stream, and the elapsed device time
  * is added per phase when the render completes. Enabling resets the counters. */
@@ -154,7 +183,8 @@ enum {
   AIR_PHASE_BALANCE = 2, /* 2:1 level balance (step iii) */
   AIR_PHASE_REFINE = 3,  /* prefix sum + child emission (step iv) */
   AIR_PHASE_OUTPUT = 4,  /* leaf compaction + band flux (step vi) */
-  AIR_N_PHASES = 5
+  AIR_PHASE_BATCH = 5,   /* the batched persistent kernel (all sweeps, all views) */
+  AIR_N_PHASES = 6
 };
 AIR_API air_status air_profile_enable(air_grid *g, int32_t on);
 /* ms[p]: summed device milliseconds, launches[p]: kernel launches, for each

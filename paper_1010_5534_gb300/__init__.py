@@ -22,7 +22,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_HERE, "libair_gb300.so")
-SOURCES = ["air_api.cu", "air_grid.cu", "air_march.cu", "air_refine.cu", "air_static.cu"]
+SOURCES = ["air_api.cu", "air_grid.cu", "air_march.cu", "air_refine.cu", "air_static.cu",
+           "air_batch.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 
@@ -31,9 +32,9 @@ AIR_OK, AIR_ERR_ARG, AIR_ERR_OOM, AIR_ERR_CUDA, AIR_ERR_CAPACITY, AIR_ERR_TIMEOU
 AIR_HOST, AIR_DEVICE = 0, 1
 
 EXPORTED = ["air_load_grid", "air_set_stream", "air_render_fixed", "air_render_adaptive",
-            "air_profile_enable", "air_profile_read", "air_band_flux_static", "air_free",
+            "air_render_batch", "air_profile_enable", "air_profile_read", "air_band_flux_static", "air_free",
             "air_last_error", "air_version"]
-PHASES = ("march", "scan", "balance", "refine", "output")
+PHASES = ("march", "scan", "balance", "refine", "output", "batch")
 
 
 def _nvcc():
@@ -99,6 +100,11 @@ class Params(C.Structure):
                 ("include_interior", C.c_int32)]
 
 
+class BatchOpts(C.Structure):
+    _fields_ = [("bands_per_thread", C.c_int32), ("use_graph", C.c_int32),
+                ("wait_timeout_ms", C.c_double), ("test_stall_barrier", C.c_int32)]
+
+
 class Image(C.Structure):
     _fields_ = [("mem", C.c_int32), ("capacity", C.c_int64), ("n_out", C.c_int64),
                 ("n_leaves", C.c_int64), ("n_rays", C.c_int64), ("n_steps", C.c_int64),
@@ -130,6 +136,10 @@ def lib():
             L.air_render_adaptive.restype = C.c_int
             L.air_render_adaptive.argtypes = [C.c_void_p, C.POINTER(View), C.POINTER(Params),
                                               C.POINTER(Image)]
+            L.air_render_batch.restype = C.c_int
+            L.air_render_batch.argtypes = [C.c_void_p, C.POINTER(View), C.c_int32,
+                                           C.POINTER(Params), C.POINTER(BatchOpts),
+                                           C.POINTER(Image)]
             L.air_profile_enable.restype = C.c_int
             L.air_profile_enable.argtypes = [C.c_void_p, C.c_int32]
             L.air_profile_read.restype = C.c_int
@@ -281,6 +291,27 @@ class Grid:
                                       C.byref(im)))
         return self._result(im, out)
 
+    def render_batch(self, views, base_res, max_level, xi_crit, xi_norm=0, refine_on=0,
+                     fp64_level=-1, include_interior=False, mem="device", fields=ALL,
+                     bands_per_thread=0, use_graph=True, wait_timeout_ms=2000.0,
+                     test_stall_barrier=False, capacity=None):
+        """Batched adaptive images of several views in one persistent launch;
+        returns one result dict per view (as render_adaptive)."""
+        _check(lib().air_set_stream(self._h, _stream()))
+        p = Params(int(base_res), int(max_level), float(xi_crit), int(xi_norm), int(refine_on),
+                   int(fp64_level), 1 if include_interior else 0)
+        o = BatchOpts(int(bands_per_thread), 1 if use_graph else 0, float(wait_timeout_ms),
+                      1 if test_stall_barrier else 0)
+        hints = getattr(self, "_batch_hint", {})
+        caps = [capacity or hints.get(k, 4 * base_res * base_res) for k in range(len(views))]
+        st, ims, outs = _batch_call(self, views, p, o, caps, mem, fields)
+        if st == AIR_ERR_CAPACITY and all(im.n_out > 0 for im in ims):
+            caps = [max(int(im.n_out), 1) for im in ims]
+            st, ims, outs = _batch_call(self, views, p, o, caps, mem, fields)
+        _check(st)
+        self._batch_hint = {k: int(im.n_out) for k, im in enumerate(ims)}
+        return [self._result(im, out) for im, out in zip(ims, outs)]
+
     def render_adaptive(self, view, base_res, max_level, xi_crit, xi_norm=0, refine_on=0,
                         fp64_level=-1, include_interior=False, mem="device", fields=ALL,
                         capacity=None):
@@ -298,6 +329,18 @@ class Grid:
         _check(st)
         self._cap_hint = max(self._cap_hint, int(im.n_out))
         return self._result(im, out)
+
+
+def _batch_call(grid, views, p, opts, caps, mem, fields):
+    ims, outs = [], []
+    for c in caps:
+        im, out = grid._alloc(c, mem, fields)
+        ims.append(im)
+        outs.append(out)
+    arr_v = (View * len(views))(*[_view(v) for v in views])
+    arr_i = (Image * len(views))(*ims)
+    st = lib().air_render_batch(grid._h, arr_v, len(views), C.byref(p), C.byref(opts), arr_i)
+    return st, arr_i, outs
 
 
 def band_flux_static(intensity, n, area0, level=None, is_leaf=None, out=None):

@@ -44,7 +44,7 @@ cudaError_t ensure(void **p, size_t *have, size_t bytes) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #x); \
   } while (0)
 
-static air_status init_scalars(Workspace &w) {
+air_status init_scalars(Workspace &w) {
   if (!w.d_total) CU_TRY(cudaMalloc((void **)&w.d_total, sizeof(int64_t)));
   if (!w.d_err) CU_TRY(cudaMalloc((void **)&w.d_err, sizeof(uint32_t)));
   if (!w.d_flux) CU_TRY(cudaMalloc((void **)&w.d_flux, sizeof(double) * (kMaxBands + 1)));
@@ -117,7 +117,7 @@ static cudaError_t regrow(T *&p, int64_t old_cap, int64_t cap, int64_t keep, int
   return cudaSuccess;
 }
 
-static air_status ensure_nodes(air_grid *g, int64_t need, int64_t keep, int64_t bound) {
+air_status ensure_nodes(air_grid *g, int64_t need, int64_t keep, int64_t bound) {
   Workspace &w = g->ws;
   const int nb = g->gv.n_bands;
   if (w.cap >= need && w.n_bands == nb) return AIR_OK;
@@ -126,6 +126,7 @@ static air_status ensure_nodes(air_grid *g, int64_t need, int64_t keep, int64_t 
   if (w.n_bands != nb) keep = 0;
   cudaStream_t st = g->stream;
   cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = regrow(w.view, w.cap, cap, keep, 1, st);
   if (e == cudaSuccess) e = regrow(w.lvl, w.cap, cap, keep, 1, st);
   if (e == cudaSuccess) e = regrow(w.pi, w.cap, cap, keep, 1, st);
   if (e == cudaSuccess) e = regrow(w.pj, w.cap, cap, keep, 1, st);
@@ -144,7 +145,7 @@ static air_status ensure_nodes(air_grid *g, int64_t need, int64_t keep, int64_t 
 static bool finite3(const double *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
 
 // Image basis: u = normalize(up x d), v = d x u, with d = normalize(dir).
-static air_status make_camera(const air_view *v, Camera &c) {
+air_status make_camera(const air_view *v, Camera &c) {
   if (!v) return set_error(AIR_ERR_ARG, "view is NULL");
   if (!finite3(v->dir) || !finite3(v->up) || !finite3(v->center) || !std::isfinite(v->half_extent) ||
       !(v->half_extent > 0.0))
@@ -238,7 +239,7 @@ static air_status finish_out(air_grid *g, air_image *im, const OutView &o, int64
   return AIR_OK;
 }
 
-static air_status check_image(const air_image *im) {
+air_status check_image(const air_image *im) {
   if (!im) return set_error(AIR_ERR_ARG, "out is NULL");
   if (im->mem != AIR_HOST && im->mem != AIR_DEVICE) return set_error(AIR_ERR_ARG, "out->mem must be AIR_HOST or AIR_DEVICE");
   if (im->capacity < 0) return set_error(AIR_ERR_ARG, "out->capacity < 0");

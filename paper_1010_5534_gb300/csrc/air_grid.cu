@@ -132,7 +132,9 @@ void dfree(T *&p) {
 void free_grid_impl(air_grid *g) {
   dfree(g->d_rho); dfree(g->d_xq); dfree(g->d_base); dfree(g->d_oct); dfree(g->d_binfo);
   dfree(g->d_table); dfree(g->d_kappa); dfree(g->d_invkappa);
+  free_batch(g);
   Workspace &w = g->ws;
+  dfree(w.view);
   dfree(w.lvl); dfree(w.pi); dfree(w.pj); dfree(w.child); dfree(w.N); dfree(w.I); dfree(w.p);
   dfree(w.steps); dfree(w.flag); dfree(w.bcount); dfree(w.boff); dfree(w.d_total); dfree(w.d_err);
   dfree(w.partial); dfree(w.d_flux); dfree(w.fN); dfree(w.fI); dfree(w.fp); dfree(w.fsteps);

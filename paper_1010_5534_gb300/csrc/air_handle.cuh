@@ -17,6 +17,7 @@ struct Workspace {
   // image quadtree
   int64_t cap = 0;
   int n_bands = 0;
+  int16_t *view = nullptr;  // view of each node (batched renders)
   int8_t *lvl = nullptr;
   int32_t *pi = nullptr, *pj = nullptr, *child = nullptr;
   float *N = nullptr, *I = nullptr, *p = nullptr;
@@ -64,6 +65,56 @@ struct Profiler {
   int64_t launches[AIR_N_PHASES] = {0};
 };
 
+struct RayGeom;
+
+// Control block of the batched persistent kernel (device memory).
+struct BatchCtl {
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  unsigned long long q_head;
+  long long n_nodes;
+  long long need;
+  int sweeps;
+  unsigned int err;
+};
+
+struct BatchArgs {
+  GridView g;
+  const RayGeom *geoms;  // [V]
+  int V, chunks, fp64_level, xi_norm, refine_on, stall;
+  double xi_crit;
+  TreeView t;
+  int16_t *view;
+  uint32_t *flag;
+  BatchCtl *ctl;
+  int32_t *bcnt;         // [blocks][V]
+  int64_t *refined;      // [V]
+  int32_t *vsweeps;      // [V]
+  long long timeout_ns;
+};
+
+// Buffers and the captured graph of batched renders.
+struct BatchWork {
+  RayGeom *geoms = nullptr;
+  BatchCtl *ctl = nullptr;
+  int32_t *bcnt = nullptr;
+  int64_t *refined = nullptr, *boff = nullptr;
+  int32_t *vsweeps = nullptr;
+  unsigned long long *vsteps = nullptr;
+  double *vflux = nullptr;
+  OutView *outs = nullptr;
+  size_t geoms_b = 0, ctl_b = 0, bcnt_b = 0, refined_b = 0, boff_b = 0, vsweeps_b = 0,
+         vsteps_b = 0, vflux_b = 0, outs_b = 0;
+  BatchCtl *h_ctl = nullptr;
+  void *h_geoms = nullptr;  // pinned staging of the per-view ray geometry
+  size_t h_geoms_b = 0;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on
+  BatchArgs key{};
+  int key_grid = 0, key_nbt = 0;
+  size_t key_smem = 0;
+};
+
 struct LastRender {
   bool valid = false;
   air_view view;
@@ -87,6 +138,7 @@ struct air_grid {
   air::Workspace ws;
   air::LastRender last;
   air::Profiler prof;
+  air::BatchWork batch;
 };
 
 namespace air {
@@ -97,4 +149,12 @@ cudaError_t prof_open(air_grid *g, int phase, int nlaunch);
 cudaError_t prof_close(air_grid *g);
 cudaError_t prof_resolve(air_grid *g);
 void free_grid_impl(air_grid *g);
+void free_batch(air_grid *g);
+// Shared by the single-view and batched renders (air_api.cu).
+air_status check_image(const air_image *im);
+air_status make_camera(const air_view *v, Camera &c);
+air_status init_scalars(Workspace &w);
+air_status ensure_nodes(air_grid *g, int64_t need, int64_t keep, int64_t bound);
+air_status render_batch(air_grid *g, const air_view *views, int32_t n_views,
+                        const air_params *params, const air_batch_opts *opts, air_image *outs);
 }  // namespace air

@@ -12,103 +12,24 @@
 // neighbour takes in the stencil.
 #include <cfloat>
 
-#include "air_refine.cuh"
+#include "air_tree.cuh"
 
 namespace air {
-
-__device__ __forceinline__ int descend(const TreeView &t, int L, int i, int j) {
-  int k = (j >> L) * t.n0 + (i >> L);
-  for (int l = 1; l <= L; ++l) {
-    const int c = t.child[k];
-    if (c < 0) break;
-    const int s = L - l;
-    k = c + ((((j >> s) & 1) << 1) | ((i >> s) & 1));
-  }
-  return k;
-}
-
-// Eq. 2 on the 3x3 stencil s[3*(dj+1) + (di+1)], FP64 with every operation
-// rounded separately (no fused multiply-add), in a fixed order.
-__device__ double xi_eq2(const double s[9], int xi_norm) {
-  const double c = s[4], xm = s[3], xp = s[5], ym = s[1], yp = s[7];
-  const double mm = s[0], pm = s[2], mp = s[6], pp = s[8];
-  const double c2 = __dmul_rn(2.0, c);
-  const double d2u = __dadd_rn(__dsub_rn(xp, c2), xm);
-  const double d2v = __dadd_rn(__dsub_rn(yp, c2), ym);
-  const double duv = __dmul_rn(__dadd_rn(__dsub_rn(__dsub_rn(pp, pm), mp), mm), 0.25);
-  const double num = __dadd_rn(__dadd_rn(__dmul_rn(d2u, d2u), __dmul_rn(d2v, d2v)),
-                               __dmul_rn(2.0, __dmul_rn(duv, duv)));
-  const double au = __dadd_rn(fabs(__dsub_rn(xp, c)), fabs(__dsub_rn(c, xm)));
-  const double av = __dadd_rn(fabs(__dsub_rn(yp, c)), fabs(__dsub_rn(c, ym)));
-  double den = __dadd_rn(__dmul_rn(au, au), __dmul_rn(av, av));
-  if (xi_norm == 1) den = __dmul_rn(2.0, den);
-  if (num == 0.0) return 0.0;
-  if (den == 0.0) return 1.0;
-  const double x = __dsqrt_rn(__ddiv_rn(num, den));
-  return x > 1.0 ? 1.0 : x;
-}
 
 // Step iii: flag every leaf below max_level whose xi >= xi_crit.
 __global__ void k_xi_scan(TreeView t, int64_t n, double xi_crit, int xi_norm, int refine_on,
                           uint32_t *__restrict__ flag) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
-  uint32_t f = 0;
-  const int L = t.lvl[k];
-  if (t.child[k] < 0 && L < t.Lm) {
-    const int i = t.pi[k], j = t.pj[k];
-    const int nl = t.n0 << L;
-    int q[9];
-#pragma unroll
-    for (int dj = -1; dj <= 1; ++dj)
-#pragma unroll
-      for (int di = -1; di <= 1; ++di) {
-        const int ii = min(max(i + di, 0), nl - 1), jj = min(max(j + dj, 0), nl - 1);
-        q[3 * (dj + 1) + (di + 1)] = (di == 0 && dj == 0) ? (int)k : descend(t, L, ii, jj);
-      }
-    double s[9];
-    if (refine_on == 0 || refine_on == 2) {
-#pragma unroll
-      for (int m = 0; m < 9; ++m) s[m] = (double)t.p[q[m]];
-      f |= xi_eq2(s, xi_norm) >= xi_crit;
-    }
-    if (refine_on == 1 || refine_on == 2) {
-#pragma unroll
-      for (int m = 0; m < 9; ++m) s[m] = (double)t.N[q[m]];
-      f |= xi_eq2(s, xi_norm) >= xi_crit;
-    }
-  }
-  flag[k] = f;
+  flag[k] = xi_flag(t, 0, k, xi_crit, xi_norm, refine_on);
 }
 
-// Step iii, balance: a flagged leaf at level L forces every leaf at a level
-// < L that covers one of its 8 same-level neighbours, and so on down the
-// levels. Each newly set flag is expanded by the thread that set it.
+// Step iii, balance closure from every flagged leaf.
 __global__ void k_balance(TreeView t, int64_t n, uint32_t *__restrict__ flag,
                           uint32_t *__restrict__ err) {
   const int64_t k0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k0 >= n || flag[k0] == 0) return;
-  int stack[kBalanceStack];
-  int sp = 0;
-  stack[sp++] = (int)k0;
-  while (sp > 0) {
-    const int q = stack[--sp];
-    const int L = t.lvl[q], i = t.pi[q], j = t.pj[q];
-    const int nl = t.n0 << L;
-    for (int dj = -1; dj <= 1; ++dj)
-      for (int di = -1; di <= 1; ++di) {
-        if (!di && !dj) continue;
-        const int ii = i + di, jj = j + dj;
-        if (ii < 0 || jj < 0 || ii >= nl || jj >= nl) continue;
-        const int m = descend(t, L, ii, jj);
-        if (t.child[m] < 0 && t.lvl[m] < L) {
-          if (atomicExch(flag + m, 1u) == 0u) {
-            if (sp < kBalanceStack) stack[sp++] = m;
-            else atomicOr(err, 1u);
-          }
-        }
-      }
-  }
+  balance_from(t, 0, (int)k0, flag, err);
 }
 
 // ---- warp-ballot prefix sums ------------------------------------------------
