@@ -174,6 +174,68 @@ AIR_API air_status air_render_batch(air_grid *g, const air_view *views, int32_t 
                                     const air_params *params, const air_batch_opts *opts,
                                     air_image *outs);
 
+/* ---- Learned refinement-depth proposal (not in the paper) ------------------
+ * A perceptron 16 -> 64 -> 64 -> 5 (ReLU) with BF16 weights and activations and
+ * FP32 accumulation predicts, per base pixel, the depth (0..4) plain AIR will
+ * refine it to. Parameters are FP32 master copies in one flat array:
+ * W1[16][64], b1[64], W2[64][64], b2[64], W3[64][5], b3[5] (input index first).
+ * Features are 16 BF16 values per sample (uint16 bit patterns). */
+#define AIR_MLP_NIN 16
+#define AIR_MLP_NHIDDEN 64
+#define AIR_MLP_NOUT 5
+#define AIR_MLP_NPARAMS (16 * 64 + 64 + 64 * 64 + 64 + 64 * 5 + 5)
+typedef struct air_mlp air_mlp;
+
+/* New network on `stream`; params (host, AIR_MLP_NPARAMS floats) or NULL for zeros. */
+AIR_API air_status air_mlp_create(const float *params, void *stream, air_mlp **out);
+AIR_API air_status air_mlp_set_stream(air_mlp *m, void *stream);
+/* Copy the parameters out (get, host) and/or replace them (set, host; resets Adam). */
+AIR_API air_status air_mlp_params(air_mlp *m, float *get, const float *set);
+/* logits[n][5] (device) for features x[n][16] (device). */
+AIR_API air_status air_mlp_forward(air_mlp *m, const uint16_t *x, int64_t n, float *logits);
+/* Mean softmax cross-entropy over n samples with labels y (device, 0..4); its
+ * gradient to grad (device, AIR_MLP_NPARAMS floats, may be NULL), the loss to
+ * *loss (host, may be NULL). */
+AIR_API air_status air_mlp_loss_grad(air_mlp *m, const uint16_t *x, const int32_t *y, int64_t n,
+                                     float *grad, double *loss);
+/* `epochs` passes of minibatch Adam (beta 0.9/0.999, eps 1e-8, learning rate lr)
+ * over the n samples; loss_history[e] (host, may be NULL) = mean loss of epoch e. */
+AIR_API air_status air_mlp_train(air_mlp *m, const uint16_t *x, const int32_t *y, int64_t n,
+                                 int32_t batch, int32_t epochs, float lr, double *loss_history);
+AIR_API void air_mlp_free(air_mlp *m);
+
+/* Training samples of one view: the 16 features of every base pixel
+ * (x[n0*n0][16], device, BF16 bits, row-major pixels) and, if y is not NULL,
+ * the depth plain AIR reaches below each base pixel (y[n0*n0], device, 0..4),
+ * taken from a plain render with `params`. */
+AIR_API air_status air_learn_samples(air_grid *g, const air_view *view, const air_params *params,
+                                     uint16_t *x, int32_t *y);
+
+typedef struct {
+  double quantile; /* propose the smallest depth whose predicted cumulative
+                      probability reaches this (0 < q <= 1; 0 = default 0.8) */
+} air_learned_opts;
+
+typedef struct {
+  int64_t proposed_rays;   /* traced in the proposal wave */
+  int64_t used_rays;       /* of those, pixels plain AIR created */
+  int64_t wasted_rays;     /* proposed but not part of the image's tree */
+  int64_t fallback_rays;   /* pixels the proposal missed, traced afterwards */
+  int32_t waves;           /* march launches: base + proposal + fallback waves */
+  int32_t sweeps;          /* refinement sweeps (as plain AIR) */
+  int64_t under_predicted; /* base pixels whose final depth exceeded the proposal */
+  int64_t over_predicted;  /* base pixels proposed deeper than needed */
+} air_learned_stats;
+
+/* Adaptive image with the learned proposal: trace the base image, run the
+ * network on its features, trace every pixel of the proposed subtrees in one
+ * wave, then run plain AIR (Section 2 steps iii-v) taking pixel values from
+ * that wave, tracing only the pixels it missed. The image (pixels, order,
+ * values) is identical to air_render_adaptive's; stats may be NULL. */
+AIR_API air_status air_render_learned(air_grid *g, const air_view *view, const air_params *params,
+                                      air_mlp *mlp, const air_learned_opts *opts, air_image *out,
+                                      air_learned_stats *stats);
+
 /* Phase profiling: when enabled, every kernel launch group of a render is
  * bracketed by CUDA events on the handle's stream, and the elapsed device time
  * is added per phase when the render completes. Enabling resets the counters. */
@@ -184,7 +246,8 @@ enum {
   AIR_PHASE_REFINE = 3,  /* prefix sum + child emission (step iv) */
   AIR_PHASE_OUTPUT = 4,  /* leaf compaction + band flux (step vi) */
   AIR_PHASE_BATCH = 5,   /* the batched persistent kernel (all sweeps, all views) */
-  AIR_N_PHASES = 6
+  AIR_PHASE_LEARN = 6,   /* features, network, proposal layout, gathers */
+  AIR_N_PHASES = 7
 };
 AIR_API air_status air_profile_enable(air_grid *g, int32_t on);
 /* ms[p]: summed device milliseconds, launches[p]: kernel launches, for each

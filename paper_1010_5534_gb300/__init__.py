@@ -23,7 +23,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_HERE, "libair_gb300.so")
 SOURCES = ["air_api.cu", "air_grid.cu", "air_march.cu", "air_refine.cu", "air_static.cu",
-           "air_batch.cu"]
+           "air_batch.cu", "air_mlp.cu", "air_learned.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 
@@ -32,9 +32,12 @@ AIR_OK, AIR_ERR_ARG, AIR_ERR_OOM, AIR_ERR_CUDA, AIR_ERR_CAPACITY, AIR_ERR_TIMEOU
 AIR_HOST, AIR_DEVICE = 0, 1
 
 EXPORTED = ["air_load_grid", "air_set_stream", "air_render_fixed", "air_render_adaptive",
-            "air_render_batch", "air_profile_enable", "air_profile_read", "air_band_flux_static", "air_free",
+            "air_render_batch", "air_mlp_create", "air_mlp_set_stream", "air_mlp_params",
+            "air_mlp_forward", "air_mlp_loss_grad", "air_mlp_train", "air_mlp_free",
+            "air_learn_samples", "air_render_learned",
+            "air_profile_enable", "air_profile_read", "air_band_flux_static", "air_free",
             "air_last_error", "air_version"]
-PHASES = ("march", "scan", "balance", "refine", "output", "batch")
+PHASES = ("march", "scan", "balance", "refine", "output", "batch", "learn")
 
 
 def _nvcc():
@@ -105,6 +108,17 @@ class BatchOpts(C.Structure):
                 ("wait_timeout_ms", C.c_double), ("test_stall_barrier", C.c_int32)]
 
 
+class LearnedOpts(C.Structure):
+    _fields_ = [("quantile", C.c_double)]
+
+
+class LearnedStats(C.Structure):
+    _fields_ = [("proposed_rays", C.c_int64), ("used_rays", C.c_int64),
+                ("wasted_rays", C.c_int64), ("fallback_rays", C.c_int64), ("waves", C.c_int32),
+                ("sweeps", C.c_int32), ("under_predicted", C.c_int64),
+                ("over_predicted", C.c_int64)]
+
+
 class Image(C.Structure):
     _fields_ = [("mem", C.c_int32), ("capacity", C.c_int64), ("n_out", C.c_int64),
                 ("n_leaves", C.c_int64), ("n_rays", C.c_int64), ("n_steps", C.c_int64),
@@ -140,6 +154,29 @@ def lib():
             L.air_render_batch.argtypes = [C.c_void_p, C.POINTER(View), C.c_int32,
                                            C.POINTER(Params), C.POINTER(BatchOpts),
                                            C.POINTER(Image)]
+            L.air_mlp_create.restype = C.c_int
+            L.air_mlp_create.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]
+            L.air_mlp_set_stream.restype = C.c_int
+            L.air_mlp_set_stream.argtypes = [C.c_void_p, C.c_void_p]
+            L.air_mlp_params.restype = C.c_int
+            L.air_mlp_params.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+            L.air_mlp_forward.restype = C.c_int
+            L.air_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]
+            L.air_mlp_loss_grad.restype = C.c_int
+            L.air_mlp_loss_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                            C.c_void_p, C.POINTER(C.c_double)]
+            L.air_mlp_train.restype = C.c_int
+            L.air_mlp_train.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
+                                        C.c_int32, C.c_float, C.c_void_p]
+            L.air_mlp_free.restype = None
+            L.air_mlp_free.argtypes = [C.c_void_p]
+            L.air_learn_samples.restype = C.c_int
+            L.air_learn_samples.argtypes = [C.c_void_p, C.POINTER(View), C.POINTER(Params),
+                                            C.c_void_p, C.c_void_p]
+            L.air_render_learned.restype = C.c_int
+            L.air_render_learned.argtypes = [C.c_void_p, C.POINTER(View), C.POINTER(Params),
+                                             C.c_void_p, C.POINTER(LearnedOpts), C.POINTER(Image),
+                                             C.POINTER(LearnedStats)]
             L.air_profile_enable.restype = C.c_int
             L.air_profile_enable.argtypes = [C.c_void_p, C.c_int32]
             L.air_profile_read.restype = C.c_int
@@ -312,6 +349,45 @@ class Grid:
         self._batch_hint = {k: int(im.n_out) for k, im in enumerate(ims)}
         return [self._result(im, out) for im, out in zip(ims, outs)]
 
+    def learn_samples(self, view, base_res, max_level, xi_crit, xi_norm=0, refine_on=0,
+                      fp64_level=-1, labels=True):
+        """(x, y): features [n0^2, 16] (BF16 bits as int16) and depth labels
+        [n0^2] (int32) of one view's base pixels, on the GPU."""
+        import torch
+        _check(lib().air_set_stream(self._h, _stream()))
+        p = Params(int(base_res), int(max_level), float(xi_crit), int(xi_norm), int(refine_on),
+                   int(fp64_level), 0)
+        nb = base_res * base_res
+        x = torch.empty((nb, 16), dtype=torch.int16, device="cuda")
+        y = torch.empty(nb, dtype=torch.int32, device="cuda") if labels else None
+        _check(lib().air_learn_samples(self._h, C.byref(_view(view)), C.byref(p),
+                                       C.c_void_p(x.data_ptr()),
+                                       C.c_void_p(y.data_ptr()) if y is not None else None))
+        return x, y
+
+    def render_learned(self, view, base_res, max_level, xi_crit, mlp, quantile=0.8, xi_norm=0,
+                       refine_on=0, fp64_level=-1, include_interior=False, mem="device",
+                       fields=ALL, capacity=None):
+        """Adaptive image with the learned proposal; returns (result, stats)."""
+        _check(lib().air_set_stream(self._h, _stream()))
+        _check(lib().air_mlp_set_stream(mlp._h, _stream()))
+        p = Params(int(base_res), int(max_level), float(xi_crit), int(xi_norm), int(refine_on),
+                   int(fp64_level), 1 if include_interior else 0)
+        o = LearnedOpts(float(quantile))
+        stats = LearnedStats()
+        cap = capacity or max(self._cap_hint, 4 * base_res * base_res)
+        im, out = self._alloc(cap, mem, fields)
+        st = lib().air_render_learned(self._h, C.byref(_view(view)), C.byref(p), mlp._h,
+                                      C.byref(o), C.byref(im), C.byref(stats))
+        if st == AIR_ERR_CAPACITY:
+            im, out = self._alloc(im.n_out, mem, fields)
+            st = lib().air_render_learned(self._h, C.byref(_view(view)), C.byref(p), mlp._h,
+                                          C.byref(o), C.byref(im), C.byref(stats))
+        _check(st)
+        self._cap_hint = max(self._cap_hint, int(im.n_out))
+        sd = {f: getattr(stats, f) for f, _ in LearnedStats._fields_}
+        return self._result(im, out), sd
+
     def render_adaptive(self, view, base_res, max_level, xi_crit, xi_norm=0, refine_on=0,
                         fp64_level=-1, include_interior=False, mem="device", fields=ALL,
                         capacity=None):
@@ -359,6 +435,68 @@ def band_flux_static(intensity, n, area0, level=None, is_leaf=None, out=None):
         C.c_void_p(out.data_ptr()), _stream())
     _check(st)
     return out
+
+
+MLP_NPARAMS = 16 * 64 + 64 + 64 * 64 + 64 + 64 * 5 + 5
+
+
+class MLP:
+    """The refinement-depth network (air_mlp_*). Features: uint16 BF16 bit
+    patterns [n, 16] on the GPU; labels int32 [n]; parameters FP32 [5573]."""
+
+    def __init__(self, params=None):
+        h = C.c_void_p()
+        arr = None
+        if params is not None:
+            arr = np.ascontiguousarray(params, dtype=np.float32)
+            assert arr.size == MLP_NPARAMS
+        _check(lib().air_mlp_create(arr.ctypes.data if arr is not None else None, _stream(),
+                                    C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().air_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self, set=None):
+        out = np.empty(MLP_NPARAMS, dtype=np.float32)
+        arr = None if set is None else np.ascontiguousarray(set, dtype=np.float32)
+        _check(lib().air_mlp_set_stream(self._h, _stream()))
+        _check(lib().air_mlp_params(self._h, out.ctypes.data,
+                                    arr.ctypes.data if arr is not None else None))
+        return out
+
+    def forward(self, x):
+        import torch
+        n = x.shape[0]
+        out = torch.empty((n, 5), dtype=torch.float32, device=x.device)
+        _check(lib().air_mlp_set_stream(self._h, _stream()))
+        _check(lib().air_mlp_forward(self._h, C.c_void_p(x.data_ptr()), n, C.c_void_p(out.data_ptr())))
+        return out
+
+    def loss_grad(self, x, y):
+        import torch
+        g = torch.empty(MLP_NPARAMS, dtype=torch.float32, device=x.device)
+        loss = C.c_double()
+        _check(lib().air_mlp_set_stream(self._h, _stream()))
+        _check(lib().air_mlp_loss_grad(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                       x.shape[0], C.c_void_p(g.data_ptr()), C.byref(loss)))
+        return loss.value, g
+
+    def train(self, x, y, batch=4096, epochs=1, lr=1e-3):
+        hist = np.zeros(max(epochs, 1))
+        _check(lib().air_mlp_set_stream(self._h, _stream()))
+        _check(lib().air_mlp_train(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                   x.shape[0], int(batch), int(epochs), float(lr),
+                                   hist.ctypes.data))
+        return hist[:epochs]
 
 
 def version() -> str:

@@ -384,6 +384,17 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
     g->last.params = key;
     g->last.n_nodes = n; g->last.n_refined = n_refined; g->last.n_sweeps = sweeps;
   }
+  return output_tree(g, cam, pr, im, n, n_refined, sweeps);
+}
+
+air_status output_tree(air_grid *g, const Camera &cam, const air_params *pr, air_image *im,
+                       int64_t n, int64_t n_refined, int32_t sweeps) {
+  air_status s = AIR_OK;
+  Workspace &w = g->ws;
+  const int nb = g->gv.n_bands;
+  cudaStream_t st = g->stream;
+  const int n0 = pr->base_res;
+  TreeView t = w.tree(n0, pr->max_level);
   // step vi: output
   const int all = pr->include_interior;
   const int64_t n_leaves = (int64_t)n0 * n0 + 3 * n_refined;

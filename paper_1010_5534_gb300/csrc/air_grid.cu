@@ -133,6 +133,7 @@ void free_grid_impl(air_grid *g) {
   dfree(g->d_rho); dfree(g->d_xq); dfree(g->d_base); dfree(g->d_oct); dfree(g->d_binfo);
   dfree(g->d_table); dfree(g->d_kappa); dfree(g->d_invkappa);
   free_batch(g);
+  free_learn(g);
   Workspace &w = g->ws;
   dfree(w.view);
   dfree(w.lvl); dfree(w.pi); dfree(w.pj); dfree(w.child); dfree(w.N); dfree(w.I); dfree(w.p);

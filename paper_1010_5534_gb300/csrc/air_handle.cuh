@@ -115,6 +115,22 @@ struct BatchWork {
   size_t key_smem = 0;
 };
 
+// Buffers of the learned-proposal render.
+struct LearnWork {
+  float *tau0 = nullptr, *xi_p = nullptr, *xi_n = nullptr, *logits = nullptr;
+  uint8_t *maxlev = nullptr;
+  uint16_t *x = nullptr;
+  int8_t *depth = nullptr, *plvl = nullptr;
+  int64_t *off = nullptr;
+  int32_t *label = nullptr, *ppi = nullptr, *ppj = nullptr, *list = nullptr;
+  float *pN = nullptr, *pI = nullptr, *pp = nullptr;
+  uint32_t *psteps = nullptr, *missing = nullptr;
+  unsigned long long *counters = nullptr;
+  size_t tau0_b = 0, xi_p_b = 0, xi_n_b = 0, logits_b = 0, maxlev_b = 0, x_b = 0, depth_b = 0,
+         plvl_b = 0, off_b = 0, label_b = 0, ppi_b = 0, ppj_b = 0, list_b = 0, pN_b = 0, pI_b = 0,
+         pp_b = 0, psteps_b = 0, missing_b = 0, counters_b = 0;
+};
+
 struct LastRender {
   bool valid = false;
   air_view view;
@@ -139,6 +155,7 @@ struct air_grid {
   air::LastRender last;
   air::Profiler prof;
   air::BatchWork batch;
+  air::LearnWork learn;
 };
 
 namespace air {
@@ -157,4 +174,10 @@ air_status init_scalars(Workspace &w);
 air_status ensure_nodes(air_grid *g, int64_t need, int64_t keep, int64_t bound);
 air_status render_batch(air_grid *g, const air_view *views, int32_t n_views,
                         const air_params *params, const air_batch_opts *opts, air_image *outs);
+air_status render_adaptive(air_grid *g, const air_view *view, const air_params *pr, air_image *im);
+// Step vi on the quadtree of nodes [0, n) in the workspace.
+air_status output_tree(air_grid *g, const Camera &cam, const air_params *pr, air_image *im,
+                       int64_t n, int64_t n_refined, int32_t sweeps);
+air_status mlp_forward(air_mlp *m, const uint16_t *x, int64_t n, float *logits, cudaStream_t st);
+void free_learn(air_grid *g);
 }  // namespace air

@@ -50,6 +50,7 @@ struct RaySource {
   const int32_t *pi, *pj;
   int64_t first, count; // rays [first, first + count) of the list / image
   int tile_w;           // grid mode: a warp covers tile_w x (32 / tile_w) pixels
+  const int32_t *list;  // nodes mode: if set, ray r is node list[r] (first ignored)
 };
 
 struct RayOut {
@@ -58,6 +59,8 @@ struct RayOut {
   int64_t stride;
   uint32_t *steps;      // [stride]
   float *p;             // [stride] band-summed intensity (NULL: written elsewhere)
+  float *tau0;          // [stride] optical depth of band 0 through the grid (optional)
+  uint8_t *maxlev;      // [stride] deepest brick level the ray crossed (optional)
 };
 
 struct MarchTune {

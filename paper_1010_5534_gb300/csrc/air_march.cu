@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kMarchBlock, MinBlocks<NBT>::value)
   int64_t k;
   if (src.mode == 0) {
     if (r >= src.count) return;
-    k = src.first + r;
+    k = src.list ? (int64_t)src.list[r] : src.first + r;
     L = src.lvl[k];
     i = src.pi[k];
     j = src.pj[k];
@@ -61,6 +61,8 @@ __global__ void __launch_bounds__(kMarchBlock, MinBlocks<NBT>::value)
   if (chunk == 0) {
     out.N[k] = st.N;
     out.steps[k] = st.steps;
+    if (out.tau0) out.tau0[k] = st.tau[0];
+    if (out.maxlev) out.maxlev[k] = (uint8_t)st.maxlev;
   }
 #pragma unroll
   for (int b = 0; b < NBT; ++b)
@@ -75,10 +77,10 @@ __global__ void __launch_bounds__(kMarchBlock, MinBlocks<NBT>::value)
 }
 
 __global__ void k_band_sum(const float *__restrict__ I, int n_bands, int64_t stride, int64_t first,
-                           int64_t count, float *__restrict__ p) {
+                           int64_t count, const int32_t *__restrict__ list, float *__restrict__ p) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= count) return;
-  const int64_t k = first + r;
+  const int64_t k = list ? (int64_t)list[r] : first + r;
   float s = 0.f;
   for (int b = 0; b < n_bands; ++b) s += I[(int64_t)b * stride + k];
   p[k] = s;
@@ -112,6 +114,11 @@ static cudaError_t launch_t(const GridView &g, const Camera &cam, const RaySourc
   if (chunks > 1 && out.p) {
     const int64_t first = src.mode == 0 ? src.first : 0;
     const int64_t count = src.mode == 0 ? src.count : (int64_t)src.n0 * src.n0;
+    if (src.list) {
+      k_band_sum<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(out.I, g.n_bands, out.stride, 0,
+                                                                  count, src.list, out.p);
+      return cudaGetLastError();
+    }
     return launch_band_sum(out.I, g.n_bands, out.stride, first, count, out.p, st);
   }
   return cudaSuccess;
@@ -131,7 +138,7 @@ cudaError_t launch_band_sum(const float *I, int n_bands, int64_t stride, int64_t
   if (count <= 0) return cudaSuccess;
   const int block = 256;
   k_band_sum<<<(unsigned)((count + block - 1) / block), block, 0, st>>>(I, n_bands, stride, first,
-                                                                       count, p);
+                                                                       count, nullptr, p);
   return cudaGetLastError();
 }
 

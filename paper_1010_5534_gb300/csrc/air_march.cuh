@@ -36,6 +36,7 @@ struct RTState {
   float N, cN;
   float tau[NBT], ctau[NBT], T[NBT], I[NBT], cI[NBT];
   uint32_t steps;
+  int maxlev;  // deepest brick level crossed
 };
 
 struct BandCtx {
@@ -55,6 +56,7 @@ __device__ __forceinline__ void rt_init(RTState<NBT> &r) {
   r.N = 0.f;
   r.cN = 0.f;
   r.steps = 0;
+  r.maxlev = 0;
 #pragma unroll
   for (int b = 0; b < NBT; ++b) {
     r.tau[b] = 0.f;
@@ -299,6 +301,7 @@ __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
       code = __ldg(g.oct + (int64_t)(-code - 1) * 8 + oc);
     }
     const int4 bi = __ldg(g.binfo + code);
+    r.maxlev = max(r.maxlev, bi.w);
     const int bo[3] = {bi.x, bi.y, bi.z};
     const int shift = Lm - bi.w;
     const int S = B << shift;

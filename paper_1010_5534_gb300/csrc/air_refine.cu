@@ -250,6 +250,13 @@ cudaError_t launch_count_flags(const uint32_t *flag, int64_t n, int32_t *bcount,
   return cudaGetLastError();
 }
 
+cudaError_t launch_scan_offsets(const int32_t *bcount, int64_t nb, int64_t *boff, int64_t *total,
+                                cudaStream_t st) {
+  if (nb == 0) return cudaMemsetAsync(total, 0, sizeof(int64_t), st);
+  k_scan_blocks<<<1, 1024, 0, st>>>(bcount, nb, boff, total);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_emit_children(const TreeView &t, const uint32_t *flag, int64_t n,
                                  const int64_t *boff, int64_t n_old, cudaStream_t st) {
   const int64_t nb = scan_blocks(n);

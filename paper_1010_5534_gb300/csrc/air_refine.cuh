@@ -58,6 +58,9 @@ cudaError_t launch_count_leaves(const TreeView &t, int all, int64_t n, int32_t *
                                 int64_t *boff, int64_t *total, cudaStream_t st);
 cudaError_t launch_emit_out(const TreeView &t, const OutView &o, int all, int64_t n,
                             const int64_t *boff, cudaStream_t st);
+// Exclusive scan of nb per-block counts (one block) -> boff, total.
+cudaError_t launch_scan_offsets(const int32_t *bcount, int64_t nb, int64_t *boff, int64_t *total,
+                                cudaStream_t st);
 int64_t flux_blocks(int64_t n);
 cudaError_t launch_flux(FluxArgs a, double *flux, double *steps, cudaStream_t st);
 
