@@ -152,6 +152,135 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _timed(fn, st):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    out = fn()
+    e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def run_batch(args):
+    """Batched AIR: the cone grid with 16 bands (0.5-10 keV) at 64 random views,
+    one persistent launch per render, against the same views one by one."""
+    import torch
+    import paper_1010_5534_gb300 as air
+    air.build()
+    W = WORKLOAD
+    sc = scenes.cone_shock_amr(W["seed"], n_base=W["n_base"], brick=W["brick"], levels=W["levels"],
+                               n_bands=16, e_lo=0.5, e_hi=10.0)
+    g = air.Grid(sc)
+    vs = scenes.random_views(3, 64)
+    st = torch.cuda.current_stream()
+    res = {}
+    for bpt in (4, 8, 16):
+        g.render_batch(vs, W["base_res"], W["max_level"], W["xi_crit"], bands_per_thread=bpt,
+                       fields=("band_flux",))
+        g.profile(True)
+        ms, b = _timed(lambda: g.render_batch(vs, W["base_res"], W["max_level"], W["xi_crit"],
+                                              bands_per_thread=bpt, fields=("band_flux",)), st)
+        prof = g.profile_read()
+        g.profile(False)
+        steps = sum(r["n_steps"] for r in b)
+        res[f"bands_per_thread_{bpt}"] = dict(ms=ms, steps=steps, steps_per_s=steps / ms * 1e3,
+                                             band_steps_per_s=16 * steps / ms * 1e3,
+                                             kernel_ms=prof["batch"][0], output_ms=prof["output"][0])
+    seq = lambda: [g.render_adaptive(v, W["base_res"], W["max_level"], W["xi_crit"],
+                                     fields=("band_flux",)) for v in vs]
+    seq()
+    ms_seq, s1 = _timed(seq, st)
+    best = min(res.values(), key=lambda r: r["ms"])
+    same = all(b["n_rays"] == a["n_rays"] and b["n_steps"] == a["n_steps"] for a, b in zip(s1, b))
+    print(json.dumps({"workload": "batch: cone grid, 64 random views x 16 bands, base 256^2, "
+                                  "max level 4, xi_crit 0.5", "rays": sum(r["n_rays"] for r in b),
+                      "steps": best["steps"], "batch": res, "sequential_ms": ms_seq,
+                      "batch_speedup_vs_sequential": ms_seq / best["ms"],
+                      "per_view_rays_and_steps_equal_to_sequential": same}), flush=True)
+
+
+def run_learned(args):
+    """Learned depth proposal: plain AIR trees of seed-varied cone grids (the
+    clumping redrawn per seed) at random views give (features, depth) samples;
+    the network is trained on the GPU with the library's kernels, then the
+    learned and plain renders are compared on held-out seeds."""
+    import torch
+    import paper_1010_5534_gb300 as air
+    from oracle import mlp as omlp
+    air.build()
+    W = WORKLOAD
+    n0, Lm, xc = W["base_res"], W["max_level"], W["xi_crit"]
+    t0 = time.perf_counter()
+    base = scenes.cone_shock_amr(0, n_base=W["n_base"], brick=W["brick"], levels=W["levels"],
+                                 keep_smooth=True)
+    xs, ys = [], []
+    gen_s = ren_s = 0.0
+    for sd in range(args.seeds):
+        t = time.perf_counter()
+        sc = scenes.reseed(base, 100 + sd)
+        gen_s += time.perf_counter() - t
+        t = time.perf_counter()
+        g = air.Grid(sc)
+        for v in scenes.random_views(5000 + sd, args.views):
+            x, y = g.learn_samples(v, n0, Lm, xc)
+            xs.append(x)
+            ys.append(y)
+        g.close()
+        torch.cuda.synchronize()
+        ren_s += time.perf_counter() - t
+    X = torch.cat(xs)
+    Y = torch.cat(ys)
+    del xs, ys
+    counts = torch.bincount(Y.long(), minlength=5).cpu().tolist()
+    net = air.MLP(omlp.init(0, scale=1.0))
+    t = time.perf_counter()
+    hist = net.train(X, Y, batch=8192, epochs=args.steps, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t
+    acc = float((net.forward(X[:2_000_000]).argmax(dim=1).to(torch.int32) == Y[:2_000_000])
+                .float().mean())
+    # held-out seeds: the benchmark view and random views
+    st = torch.cuda.current_stream()
+    evals = []
+    for sd in range(3):
+        sc = scenes.reseed(base, 900 + sd)
+        g = air.Grid(sc)
+        for v in [scenes.axis_view("+z")] + scenes.random_views(9000 + sd, 3):
+            for _ in range(2):
+                g.render_adaptive(v, n0, Lm, xc)
+                g.render_learned(v, n0, Lm, xc, net, quantile=0.8)
+            ms_p, rp = _timed(lambda: g.render_adaptive(v, n0, Lm, xc), st)
+            ms_l, (rl, stl) = _timed(lambda: g.render_learned(v, n0, Lm, xc, net, quantile=0.8), st)
+            same = all(bool((rp[k] == rl[k]).all()) for k in ("level", "i", "j", "intensity"))
+            evals.append(dict(view=list(v.dir), plain_ms=ms_p, learned_ms=ms_l,
+                              plain_waves=1 + rp["n_sweeps"], learned_waves=stl["waves"],
+                              rays=rp["n_rays"], proposed=stl["proposed_rays"],
+                              wasted=stl["wasted_rays"], fallback=stl["fallback_rays"],
+                              under=stl["under_predicted"], over=stl["over_predicted"],
+                              identical=same))
+        g.close()
+    nb = n0 * n0
+    print(json.dumps({
+        "workload": f"learned proposal: {args.seeds} seeds x {args.views} views = "
+                    f"{args.seeds * args.views} plain trees of the cone grid (clumping redrawn "
+                    f"per seed), base {n0}^2, max level {Lm}, xi_crit {xc}",
+        "samples": int(X.shape[0]), "label_counts": counts, "epochs": args.steps,
+        "loss_history": [float(h) for h in hist], "train_s": train_s, "data_gen_s": gen_s,
+        "data_render_s": ren_s, "train_accuracy": acc,
+        "heldout": evals,
+        "heldout_mean": {
+            "plain_ms": float(np.mean([e["plain_ms"] for e in evals])),
+            "learned_ms": float(np.mean([e["learned_ms"] for e in evals])),
+            "plain_waves": float(np.mean([e["plain_waves"] for e in evals])),
+            "learned_waves": float(np.mean([e["learned_waves"] for e in evals])),
+            "misprediction_rate": float(np.mean([(e["under"] + e["over"]) / nb for e in evals])),
+            "under_rate": float(np.mean([e["under"] / nb for e in evals])),
+            "wasted_fraction": float(np.mean([e["wasted"] / e["rays"] for e in evals])),
+            "all_identical": all(e["identical"] for e in evals)},
+        "total_s": time.perf_counter() - t0}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -159,12 +288,22 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="air", choices=["air", "batch", "learned"],
+                    help="air: the benchmark line (one adaptive image of the cone grid); "
+                         "batch: 64 views x 16 bands in one persistent launch vs one by one; "
+                         "learned: train the depth network on 2000 plain trees, evaluate")
+    ap.add_argument("--seeds", type=int, default=40)
+    ap.add_argument("--views", type=int, default=50)
     ap.add_argument("--profile-case", action="store_true",
                     help="one adaptive image of the workload after --warmup images, then exit "
                          "(the case profiled with ncu)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "learned":
+        return run_learned(args)
     assert args.warmup >= 3 or args.profile_case, "at least 3 warm-up steps"
 
     import torch

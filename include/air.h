@@ -122,6 +122,21 @@ typedef struct {
   double *band_flux;   /* [n_bands] sum over leaves of I_b x pixel area, optional */
 } air_image;
 
+/* Launch configuration of a grid handle (air_autotune, air_set_tuning). Every
+ * field only changes how work maps to GPU threads, never the results; 0 means
+ * the library default. */
+typedef struct {
+  int32_t tile_w;                 /* fixed images: a warp traces tile_w x (32 / tile_w)
+                                     pixels (1, 2, 4, 8, 16, 32; default 8) */
+  int32_t bands_per_thread;       /* single-view renders: bands one thread carries
+                                     along a ray (1, 2, 4, 8, 16; default all up to 16) */
+  int32_t batch_bands_per_thread; /* batched renders (default 8 for more than 4 bands) */
+  int32_t batch_blocks_per_sm;    /* persistent CTAs per SM of batched renders
+                                     (default: as many as fit) */
+  double best_ms[3];              /* out of air_autotune: fixed, adaptive, batched time */
+  int32_t trials;                 /* out of air_autotune: configurations timed */
+} air_tuning;
+
 typedef struct air_grid air_grid;
 
 /* Copy a grid to the device and build its brick lookup (Section 2 step i).
@@ -235,6 +250,16 @@ typedef struct {
 AIR_API air_status air_render_learned(air_grid *g, const air_view *view, const air_params *params,
                                       air_mlp *mlp, const air_learned_opts *opts, air_image *out,
                                       air_learned_stats *stats);
+
+/* Autotuner (not in the paper): time candidate launch configurations on this
+ * grid with this view and parameters (fixed image of up to 2048^2 pixels,
+ * adaptive image, and, if n_views_batch > 0, a batch of that many copies of the
+ * view), keep the fastest per knob in the handle and return it in *out (may be
+ * NULL). Later renders on the handle use it. */
+AIR_API air_status air_autotune(air_grid *g, const air_view *view, const air_params *params,
+                                int32_t n_views_batch, air_tuning *out);
+AIR_API air_status air_set_tuning(air_grid *g, const air_tuning *t);
+AIR_API air_status air_get_tuning(air_grid *g, air_tuning *t);
 
 /* Phase profiling: when enabled, every kernel launch group of a render is
  * bracketed by CUDA events on the handle's stream, and the elapsed device time

@@ -23,7 +23,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_HERE, "libair_gb300.so")
 SOURCES = ["air_api.cu", "air_grid.cu", "air_march.cu", "air_refine.cu", "air_static.cu",
-           "air_batch.cu", "air_mlp.cu", "air_learned.cu"]
+           "air_batch.cu", "air_mlp.cu", "air_learned.cu", "air_tune.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 
@@ -34,7 +34,8 @@ AIR_HOST, AIR_DEVICE = 0, 1
 EXPORTED = ["air_load_grid", "air_set_stream", "air_render_fixed", "air_render_adaptive",
             "air_render_batch", "air_mlp_create", "air_mlp_set_stream", "air_mlp_params",
             "air_mlp_forward", "air_mlp_loss_grad", "air_mlp_train", "air_mlp_free",
-            "air_learn_samples", "air_render_learned",
+            "air_learn_samples", "air_render_learned", "air_autotune", "air_set_tuning",
+            "air_get_tuning",
             "air_profile_enable", "air_profile_read", "air_band_flux_static", "air_free",
             "air_last_error", "air_version"]
 PHASES = ("march", "scan", "balance", "refine", "output", "batch", "learn")
@@ -108,6 +109,12 @@ class BatchOpts(C.Structure):
                 ("wait_timeout_ms", C.c_double), ("test_stall_barrier", C.c_int32)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("bands_per_thread", C.c_int32),
+                ("batch_bands_per_thread", C.c_int32), ("batch_blocks_per_sm", C.c_int32),
+                ("best_ms", C.c_double * 3), ("trials", C.c_int32)]
+
+
 class LearnedOpts(C.Structure):
     _fields_ = [("quantile", C.c_double)]
 
@@ -177,6 +184,13 @@ def lib():
             L.air_render_learned.argtypes = [C.c_void_p, C.POINTER(View), C.POINTER(Params),
                                              C.c_void_p, C.POINTER(LearnedOpts), C.POINTER(Image),
                                              C.POINTER(LearnedStats)]
+            L.air_autotune.restype = C.c_int
+            L.air_autotune.argtypes = [C.c_void_p, C.POINTER(View), C.POINTER(Params), C.c_int32,
+                                       C.POINTER(Tuning)]
+            L.air_set_tuning.restype = C.c_int
+            L.air_set_tuning.argtypes = [C.c_void_p, C.POINTER(Tuning)]
+            L.air_get_tuning.restype = C.c_int
+            L.air_get_tuning.argtypes = [C.c_void_p, C.POINTER(Tuning)]
             L.air_profile_enable.restype = C.c_int
             L.air_profile_enable.argtypes = [C.c_void_p, C.c_int32]
             L.air_profile_read.restype = C.c_int
@@ -275,6 +289,24 @@ class Grid:
             self.close()
         except Exception:
             pass
+
+    def autotune(self, view, base_res, max_level, xi_crit, n_views_batch=0, xi_norm=0,
+                 refine_on=0, fp64_level=-1):
+        """Time launch configurations on this grid and keep the fastest."""
+        _check(lib().air_set_stream(self._h, _stream()))
+        p = Params(int(base_res), int(max_level), float(xi_crit), int(xi_norm), int(refine_on),
+                   int(fp64_level), 0)
+        t = Tuning()
+        _check(lib().air_autotune(self._h, C.byref(_view(view)), C.byref(p), int(n_views_batch),
+                                  C.byref(t)))
+        return {f: (list(getattr(t, f)) if f == "best_ms" else getattr(t, f))
+                for f, _ in Tuning._fields_}
+
+    def set_tuning(self, tile_w=0, bands_per_thread=0, batch_bands_per_thread=0,
+                   batch_blocks_per_sm=0):
+        t = Tuning(int(tile_w), int(bands_per_thread), int(batch_bands_per_thread),
+                   int(batch_blocks_per_sm))
+        _check(lib().air_set_tuning(self._h, C.byref(t)))
 
     def profile(self, on=True):
         """Enable (and reset) or disable per-phase device timing."""

@@ -167,10 +167,11 @@ air_status make_camera(const air_view *v, Camera &c) {
   return AIR_OK;
 }
 
-static MarchTune default_tune(int fp64_level) {
+MarchTune march_tune(const air_grid *g, int fp64_level) {
   MarchTune t;
   t.block = 128;
   t.fp64_level = fp64_level < 0 ? 3 : fp64_level;
+  t.nbt = g->tune.bands_per_thread;
   return t;
 }
 
@@ -266,11 +267,12 @@ air_status render_fixed(air_grid *g, const air_view *view, int32_t res, int32_t 
   CU_TRY(ensure((void **)&w.partial, &w.partial_b, sizeof(double) * (nb + 1) * flux_blocks(n)));
   cudaStream_t st = g->stream;
   RaySource src{};
-  src.mode = 1; src.n0 = res; src.first = 0; src.count = n; src.tile_w = 8;
+  src.mode = 1; src.n0 = res; src.first = 0; src.count = n;
+  src.tile_w = g->tune.tile_w > 0 ? g->tune.tile_w : 8;
   RayOut ro{w.fN, w.fI, n, w.fsteps, w.fp};
   g->prof.used = 0;
-  CU_TRY(prof_open(g, AIR_PHASE_MARCH, nb > 16 ? 2 : 1));
-  CU_TRY(launch_march(g->gv, cam, src, ro, default_tune(fp64_level), st));
+  CU_TRY(prof_open(g, AIR_PHASE_MARCH, nb > (g->tune.bands_per_thread > 0 ? g->tune.bands_per_thread : 16) ? 2 : 1));
+  CU_TRY(launch_march(g->gv, cam, src, ro, march_tune(g, fp64_level), st));
   CU_TRY(prof_close(g));
   FluxArgs fa{};
   fa.n = n; fa.child = nullptr; fa.lvl = nullptr; fa.I = w.fI; fa.stride = n; fa.steps = w.fsteps;
@@ -327,9 +329,10 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
     const int64_t nbase = (int64_t)n0 * n0;
     if ((s = ensure_nodes(g, std::min<int64_t>(bound, std::max<int64_t>(4 * nbase, w.cap)), 0, bound))) return s;
     t = w.tree(n0, Lm);
-    const MarchTune tune = default_tune(pr->fp64_level);
+    const MarchTune tune = march_tune(g, pr->fp64_level);
     g->prof.used = 0;
-    const int march_launches = nb > 16 ? 2 : 1;  // march (+ band sum when bands are chunked)
+    const int nbt_eff = tune.nbt > 0 ? tune.nbt : (nb < 16 ? nb : 16);
+    const int march_launches = nb > nbt_eff ? 2 : 1;  // march (+ band sum when bands are chunked)
     // step i + ii: base image
     CU_TRY(prof_open(g, AIR_PHASE_REFINE, 1));
     CU_TRY(launch_init_base(t, st));

@@ -463,7 +463,8 @@ air_status render_batch(air_grid *g, const air_view *views, int32_t V, const air
   if (opts) op = *opts;
   if (!(op.wait_timeout_ms > 0.0)) op.wait_timeout_ms = 2000.0;
   const int nb = g->gv.n_bands;
-  int nbt = op.bands_per_thread > 0 ? op.bands_per_thread : default_bands_per_thread(nb);
+  int nbt = op.bands_per_thread > 0 ? op.bands_per_thread
+            : (g->tune.batch_bands_per_thread > 0 ? g->tune.batch_bands_per_thread : default_bands_per_thread(nb));
   BatchOccFn occ;
   BatchLaunchFn launch;
   if (!batch_fns(nbt, g->gv.kind == AIR_GRID_AMR, &occ, &launch))
@@ -497,6 +498,7 @@ air_status render_batch(air_grid *g, const air_view *views, int32_t V, const air
   CU_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   CU_TRY(occ(&per_sm, smem));
   if (per_sm < 1) return set_error(AIR_ERR_CUDA, "batched kernel cannot be resident (smem %zu B)", smem);
+  if (g->tune.batch_blocks_per_sm > 0 && g->tune.batch_blocks_per_sm < per_sm) per_sm = g->tune.batch_blocks_per_sm;
   const int grid = per_sm * sms;
   // device-side state
   CU_TRY(ensure((void **)&bw.geoms, &bw.geoms_b, sizeof(RayGeom) * V));

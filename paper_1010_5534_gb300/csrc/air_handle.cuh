@@ -156,6 +156,7 @@ struct air_grid {
   air::Profiler prof;
   air::BatchWork batch;
   air::LearnWork learn;
+  air_tuning tune{};  // launch configuration (air_autotune / air_set_tuning)
 };
 
 namespace air {
@@ -179,5 +180,9 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
 air_status output_tree(air_grid *g, const Camera &cam, const air_params *pr, air_image *im,
                        int64_t n, int64_t n_refined, int32_t sweeps);
 air_status mlp_forward(air_mlp *m, const uint16_t *x, int64_t n, float *logits, cudaStream_t st);
+// The march configuration of this handle's tuning.
+MarchTune march_tune(const air_grid *g, int fp64_level);
+air_status render_fixed(air_grid *g, const air_view *view, int32_t res, int32_t fp64_level,
+                        air_image *im);
 void free_learn(air_grid *g);
 }  // namespace air

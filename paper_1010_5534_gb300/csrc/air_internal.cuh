@@ -66,6 +66,7 @@ struct RayOut {
 struct MarchTune {
   int block;            // threads per block
   int fp64_level;       // bricks at this level or deeper use FP64 entry/exit
+  int nbt;              // bands one thread carries (1, 2, 4, 8, 16; 0 = all up to 16)
 };
 
 // Kahan-compensated sum: s += x with running compensation c.

@@ -126,10 +126,12 @@ static cudaError_t launch_t(const GridView &g, const Camera &cam, const RaySourc
 
 cudaError_t launch_march(const GridView &g, const Camera &cam, const RaySource &src,
                          const RayOut &out, const MarchTune &tune, cudaStream_t st) {
-  if (g.n_bands <= 1) return launch_t<1>(g, cam, src, out, tune, st);
-  if (g.n_bands <= 2) return launch_t<2>(g, cam, src, out, tune, st);
-  if (g.n_bands <= 4) return launch_t<4>(g, cam, src, out, tune, st);
-  if (g.n_bands <= 8) return launch_t<8>(g, cam, src, out, tune, st);
+  int nbt = tune.nbt;
+  if (nbt <= 0) nbt = g.n_bands;
+  if (nbt <= 1) return launch_t<1>(g, cam, src, out, tune, st);
+  if (nbt <= 2) return launch_t<2>(g, cam, src, out, tune, st);
+  if (nbt <= 4) return launch_t<4>(g, cam, src, out, tune, st);
+  if (nbt <= 8) return launch_t<8>(g, cam, src, out, tune, st);
   return launch_t<16>(g, cam, src, out, tune, st);
 }
 

@@ -196,7 +196,7 @@ def cone_shock_amr(seed: int = 0, n_base: int = 128, brick: int = 16, levels: in
                    thickness: float = 0.04, apex=(-0.5, 0.0, 0.0),
                    star=(-0.8, 0.0, 0.0), clump_sigma: float = 0.3,
                    clump_scale: float = 0.0, n_tbins: int = 64,
-                   refine_margin: float = 1.0) -> Scene:
+                   refine_margin: float = 1.0, keep_smooth: bool = False) -> Scene:
     """Block-AMR grid over [-1,1]^3: n_base^3 base cells in brick^3 bricks,
     `levels` refinement levels (factor 2) on bricks near a conical shock
     (apex `apex`, axis +x, half-angle 30 deg, shell thickness 0.04 = 0.02 of the
@@ -258,6 +258,7 @@ def cone_shock_amr(seed: int = 0, n_base: int = 128, brick: int = 16, levels: in
     rho = np.empty((nb, brick, brick, brick), dtype=np.float32)
     temp = np.empty((nb, brick, brick, brick), dtype=np.float32)
     off = np.arange(brick) + 0.5
+    smooth = np.empty(rho.shape, dtype=np.float64) if keep_smooth else None
     if clump_scale > 0:
         nl = int(math.ceil((hi - lo) / clump_scale)) + 2
         lattice = rng.standard_normal((nl, nl, nl))
@@ -289,15 +290,36 @@ def cone_shock_amr(seed: int = 0, n_base: int = 128, brick: int = 16, levels: in
                 z = cell_noise[sel]
             clump = np.exp(clump_sigma * z - 0.5 * clump_sigma ** 2)
             rho[sel] = (rho_w * fac * clump).astype(np.float32)
+            if keep_smooth:
+                smooth[sel] = rho_w * fac
             temp[sel] = np.where(shell, 10.0 ** 7.5, 1e4).astype(np.float32)
 
     edges = band_edges(n_bands, e_lo, e_hi)
-    return Scene(kind="amr", lo=(lo,) * 3, hi=(hi,) * 3, n=(n_base,) * 3, rho=rho, temp=temp,
+    sc = Scene(kind="amr", lo=(lo,) * 3, hi=(hi,) * 3, n=(n_base,) * 3, rho=rho, temp=temp,
                  brick=brick, max_level=levels, brick_level=levels_arr,
                  brick_origin=origins.astype(np.int32), emis_mode=1,
                  lambda_table=cooling_table(edges, n_tbins), logT_lo=4.0, logT_hi=9.0,
                  kappa=band_kappa(edges, kappa0),
                  name=f"cone_amr_{n_base}^3_b{brick}_L{levels}_{n_bands}band_c{clump_scale}_s{seed}")
+    if keep_smooth:
+        sc.rho_smooth = smooth
+        sc.clump_sigma = clump_sigma
+    return sc
+
+
+def reseed(scene: Scene, seed: int) -> Scene:
+    """The same cone-shock grid with the per-cell clumping redrawn from `seed`
+    (equal to cone_shock_amr(seed, ...) with the same other arguments, whose
+    brick layout draws no random numbers). Needs a scene made with
+    keep_smooth=True and clump_scale=0."""
+    import copy
+    rng = np.random.Generator(np.random.PCG64(seed))
+    z = rng.standard_normal(scene.rho_smooth.size).reshape(scene.rho_smooth.shape)
+    sig = scene.clump_sigma
+    out = copy.copy(scene)
+    out.rho = (scene.rho_smooth * np.exp(sig * z - 0.5 * sig ** 2)).astype(np.float32)
+    out.name = scene.name.rsplit("_s", 1)[0] + f"_s{seed}"
+    return out
 
 
 # --------------------------------------------------------------------------

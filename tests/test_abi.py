@@ -78,6 +78,20 @@ int main(void) {
   F(air_image, n_rays) F(air_image, n_steps) F(air_image, n_sweeps) F(air_image, level)
   F(air_image, i) F(air_image, j) F(air_image, is_leaf) F(air_image, coldens)
   F(air_image, intensity) F(air_image, p) F(air_image, band_flux)
+  printf("air_batch_opts %zu\n", sizeof(air_batch_opts));
+  F(air_batch_opts, bands_per_thread) F(air_batch_opts, use_graph)
+  F(air_batch_opts, wait_timeout_ms) F(air_batch_opts, test_stall_barrier)
+  printf("air_learned_opts %zu\n", sizeof(air_learned_opts));
+  F(air_learned_opts, quantile)
+  printf("air_learned_stats %zu\n", sizeof(air_learned_stats));
+  F(air_learned_stats, proposed_rays) F(air_learned_stats, used_rays)
+  F(air_learned_stats, wasted_rays) F(air_learned_stats, fallback_rays)
+  F(air_learned_stats, waves) F(air_learned_stats, sweeps)
+  F(air_learned_stats, under_predicted) F(air_learned_stats, over_predicted)
+  printf("air_tuning %zu\n", sizeof(air_tuning));
+  F(air_tuning, tile_w) F(air_tuning, bands_per_thread) F(air_tuning, batch_bands_per_thread)
+  F(air_tuning, batch_blocks_per_sm) F(air_tuning, best_ms) F(air_tuning, trials)
+  printf("AIR_MLP_NPARAMS %d\n", AIR_MLP_NPARAMS);
   return 0;
 }
 '''
@@ -92,7 +106,10 @@ def test_struct_layouts_match_header(tmp_path):
     lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     got = dict(l.split() for l in lines if l.strip())
     mapping = {"air_grid_desc": air.GridDesc, "air_view": air.View, "air_params": air.Params,
-               "air_image": air.Image}
+               "air_image": air.Image, "air_batch_opts": air.BatchOpts,
+               "air_learned_opts": air.LearnedOpts, "air_learned_stats": air.LearnedStats,
+               "air_tuning": air.Tuning}
+    assert int(got["AIR_MLP_NPARAMS"]) == air.MLP_NPARAMS
     for cname, cls in mapping.items():
         assert C.sizeof(cls) == int(got[cname]), cname
         for f, _ in cls._fields_:
