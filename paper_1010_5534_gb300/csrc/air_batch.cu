@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kBatchBlock) k_air_batch(BatchArgs a) {
   int32_t *cnt = (int32_t *)(vbase + V);
   int32_t *wcnt = cnt + V;
   __shared__ int64_t s_total;
-  if (g.emis_mode)
+  if (g.cell_fmt == kCellXq)
     for (int x = threadIdx.x; x < nb * tstride; x += blockDim.x) tab[x] = g.table[x];
   __syncthreads();
 
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(kBatchBlock) k_air_batch(BatchArgs a) {
         bc.tab = tab + b0 * tstride;
         bc.tstride = tstride;
         bc.nbh = min(NBT, nb - b0);
-        bc.emis = g.emis_mode;
+        bc.fmt = g.cell_fmt;
         BandRegs<NBT> br;
 #pragma unroll
         for (int q = 0; q < NBT; ++q) {

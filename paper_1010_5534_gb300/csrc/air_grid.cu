@@ -21,24 +21,39 @@
 
 namespace air {
 
+// Raw fields -> cell records (see GridView::cell_fmt). The table coordinate
+// of T is x = (log10 T - logT_lo) / dlogT * (n_tbins - 1), clamped; for one
+// band, Lambda = (1 - w) tab[k] + w tab[k + 1] with k = floor(x) (at most
+// n_tbins - 2) and w = x - k, in FP64, rounded once to FP32.
 template <typename T>
 __global__ void k_convert_fields(const T *__restrict__ rho_in, const T *__restrict__ t_in,
-                                 int64_t n, float *__restrict__ rho, uint32_t *__restrict__ xq,
-                                 double logT_lo, double dlogT, int n_tbins,
+                                 int64_t n, int fmt, void *__restrict__ out, double logT_lo,
+                                 double dlogT, int n_tbins, const float *__restrict__ tab0,
                                  unsigned long long *__restrict__ bad) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const double r = (double)rho_in[k];
   bool ok = isfinite(r) && r >= 0.0;
-  rho[k] = ok ? (float)r : 0.f;
-  if (t_in) {
-    const double T = (double)t_in[k];
-    const bool tok = isfinite(T) && T > 0.0;
+  const float rf = ok ? (float)r : 0.f;
+  if (fmt == kCellRho) {
+    ((float *)out)[k] = rf;
+  } else {
+    const double Tv = (double)t_in[k];
+    const bool tok = isfinite(Tv) && Tv > 0.0;
     ok = ok && tok;
-    double x = tok ? (log10(T) - logT_lo) / dlogT * (double)(n_tbins - 1) : 0.0;
+    double x = tok ? (log10(Tv) - logT_lo) / dlogT * (double)(n_tbins - 1) : 0.0;
     if (!(x > 0.0)) x = 0.0;
     if (x > (double)(n_tbins - 1)) x = (double)(n_tbins - 1);
-    xq[k] = (uint32_t)rint(x * (double)(1u << kXqFracBits));
+    uint32_t aux;
+    if (fmt == kCellLam) {
+      int kk = (int)floor(x);
+      if (kk > n_tbins - 2) kk = n_tbins - 2;
+      const double w = x - (double)kk;
+      aux = __float_as_uint((float)((1.0 - w) * (double)tab0[kk] + w * (double)tab0[kk + 1]));
+    } else {
+      aux = (uint32_t)rint(x * (double)(1u << kXqFracBits));
+    }
+    ((uint2 *)out)[k] = make_uint2(__float_as_uint(rf), aux);
   }
   if (!ok) atomicAdd(bad, 1ull);
 }
@@ -130,7 +145,7 @@ void dfree(T *&p) {
 }  // namespace
 
 void free_grid_impl(air_grid *g) {
-  dfree(g->d_rho); dfree(g->d_xq); dfree(g->d_base); dfree(g->d_oct); dfree(g->d_binfo);
+  dfree(g->d_cells); dfree(g->d_base); dfree(g->d_oct); dfree(g->d_binfo);
   dfree(g->d_table); dfree(g->d_kappa); dfree(g->d_invkappa);
   free_batch(g);
   free_learn(g);
@@ -211,64 +226,7 @@ air_status load_grid_impl(const air_grid_desc *d, air_grid *g) {
   v.n_tbins = d->emis_mode == 1 ? d->n_tbins : 1;
   g->n_cells = n_cells;
 
-  // ---- device copies
-  cudaStream_t st = g->stream;
-  CU_TRY(cudaMalloc((void **)&g->d_rho, sizeof(float) * n_cells));
-  if (d->emis_mode == 1) CU_TRY(cudaMalloc((void **)&g->d_xq, sizeof(uint32_t) * n_cells));
-  {
-    const size_t es = d->field_dtype == AIR_F64 ? 8 : 4;
-    void *raw_r = nullptr, *raw_t = nullptr;
-    unsigned long long *d_bad = nullptr, h_bad = 0;
-    // convert in slices so the staging buffer stays bounded
-    const int64_t slice = (int64_t)1 << 26;
-    const int64_t sl = std::min<int64_t>(slice, n_cells);
-    cudaError_t e = cudaMalloc(&raw_r, es * sl);
-    if (e == cudaSuccess && d->emis_mode == 1) e = cudaMalloc(&raw_t, es * sl);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&d_bad, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), st);
-    for (int64_t off = 0; e == cudaSuccess && off < n_cells; off += sl) {
-      const int64_t m = std::min<int64_t>(sl, n_cells - off);
-      e = cudaMemcpyAsync(raw_r, (const char *)d->rho + es * off, es * m, cudaMemcpyHostToDevice, st);
-      if (e == cudaSuccess && raw_t)
-        e = cudaMemcpyAsync(raw_t, (const char *)d->temp + es * off, es * m, cudaMemcpyHostToDevice, st);
-      if (e != cudaSuccess) break;
-      const unsigned blocks = (unsigned)((m + 255) / 256);
-      const double dlogT = d->logT_hi - d->logT_lo;
-      uint32_t *xq = raw_t ? g->d_xq + off : nullptr;
-      if (d->field_dtype == AIR_F64)
-        k_convert_fields<double><<<blocks, 256, 0, st>>>((const double *)raw_r, (const double *)raw_t, m,
-                                                         g->d_rho + off, xq, d->logT_lo, dlogT, d->n_tbins, d_bad);
-      else
-        k_convert_fields<float><<<blocks, 256, 0, st>>>((const float *)raw_r, (const float *)raw_t, m,
-                                                        g->d_rho + off, xq, d->logT_lo, dlogT, d->n_tbins, d_bad);
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, d_bad, sizeof(h_bad), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(raw_r);
-    if (raw_t) cudaFree(raw_t);
-    if (d_bad) cudaFree(d_bad);
-    if (e != cudaSuccess) return cuda_fail(e, "field upload");
-    if (h_bad) return set_error(AIR_ERR_ARG, "%llu cells have rho < 0, T <= 0 or a non-finite value", h_bad);
-  }
-  v.rho = g->d_rho;
-  v.xq = g->d_xq;
-  if (d->kind == AIR_GRID_AMR) {
-    std::vector<int4> bi(d->n_bricks);
-    for (int b = 0; b < d->n_bricks; ++b)
-      bi[b] = make_int4(d->brick_origin[3 * b], d->brick_origin[3 * b + 1], d->brick_origin[3 * b + 2], d->brick_level[b]);
-    CU_TRY(cudaMalloc((void **)&g->d_base, sizeof(int32_t) * ob.base.size()));
-    CU_TRY(cudaMemcpy(g->d_base, ob.base.data(), sizeof(int32_t) * ob.base.size(), cudaMemcpyHostToDevice));
-    if (!ob.oct.empty()) {
-      CU_TRY(cudaMalloc((void **)&g->d_oct, sizeof(int32_t) * ob.oct.size()));
-      CU_TRY(cudaMemcpy(g->d_oct, ob.oct.data(), sizeof(int32_t) * ob.oct.size(), cudaMemcpyHostToDevice));
-    }
-    CU_TRY(cudaMalloc((void **)&g->d_binfo, sizeof(int4) * bi.size()));
-    CU_TRY(cudaMemcpy(g->d_binfo, bi.data(), sizeof(int4) * bi.size(), cudaMemcpyHostToDevice));
-    v.base = g->d_base;
-    v.oct = g->d_oct;
-    v.binfo = g->d_binfo;
-  }
+  // ---- device copies: emission table first (the upload of one-band grids uses it)
   {
     const int ts = v.n_tbins + 1;
     std::vector<float> tab((size_t)d->n_bands * ts, 0.f), kap(d->n_bands), ik(d->n_bands);
@@ -290,6 +248,65 @@ air_status load_grid_impl(const air_grid_desc *d, air_grid *g) {
     v.table = g->d_table;
     v.kappa = g->d_kappa;
     v.invkappa = g->d_invkappa;
+  }
+  cudaStream_t st = g->stream;
+  v.cell_fmt = d->emis_mode == 0 ? kCellRho : (d->n_bands == 1 ? kCellLam : kCellXq);
+  CU_TRY(cudaMalloc(&g->d_cells, (v.cell_fmt == kCellRho ? sizeof(float) : sizeof(uint2)) * n_cells));
+  {
+    const size_t es = d->field_dtype == AIR_F64 ? 8 : 4;
+    void *raw_r = nullptr, *raw_t = nullptr;
+    unsigned long long *d_bad = nullptr, h_bad = 0;
+    // convert in slices so the staging buffer stays bounded
+    const int64_t slice = (int64_t)1 << 26;
+    const int64_t sl = std::min<int64_t>(slice, n_cells);
+    cudaError_t e = cudaMalloc(&raw_r, es * sl);
+    if (e == cudaSuccess && d->emis_mode == 1) e = cudaMalloc(&raw_t, es * sl);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d_bad, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), st);
+    for (int64_t off = 0; e == cudaSuccess && off < n_cells; off += sl) {
+      const int64_t m = std::min<int64_t>(sl, n_cells - off);
+      e = cudaMemcpyAsync(raw_r, (const char *)d->rho + es * off, es * m, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess && raw_t)
+        e = cudaMemcpyAsync(raw_t, (const char *)d->temp + es * off, es * m, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) break;
+      const unsigned blocks = (unsigned)((m + 255) / 256);
+      const double dlogT = d->logT_hi - d->logT_lo;
+      void *dst = v.cell_fmt == kCellRho ? (void *)((float *)g->d_cells + off)
+                                         : (void *)((uint2 *)g->d_cells + off);
+      if (d->field_dtype == AIR_F64)
+        k_convert_fields<double><<<blocks, 256, 0, st>>>((const double *)raw_r, (const double *)raw_t, m,
+                                                         v.cell_fmt, dst, d->logT_lo, dlogT, d->n_tbins,
+                                                         g->d_table, d_bad);
+      else
+        k_convert_fields<float><<<blocks, 256, 0, st>>>((const float *)raw_r, (const float *)raw_t, m,
+                                                        v.cell_fmt, dst, d->logT_lo, dlogT, d->n_tbins,
+                                                        g->d_table, d_bad);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, d_bad, sizeof(h_bad), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(raw_r);
+    if (raw_t) cudaFree(raw_t);
+    if (d_bad) cudaFree(d_bad);
+    if (e != cudaSuccess) return cuda_fail(e, "field upload");
+    if (h_bad) return set_error(AIR_ERR_ARG, "%llu cells have rho < 0, T <= 0 or a non-finite value", h_bad);
+  }
+  v.cells = g->d_cells;
+  if (d->kind == AIR_GRID_AMR) {
+    std::vector<int4> bi(d->n_bricks);
+    for (int b = 0; b < d->n_bricks; ++b)
+      bi[b] = make_int4(d->brick_origin[3 * b], d->brick_origin[3 * b + 1], d->brick_origin[3 * b + 2], d->brick_level[b]);
+    CU_TRY(cudaMalloc((void **)&g->d_base, sizeof(int32_t) * ob.base.size()));
+    CU_TRY(cudaMemcpy(g->d_base, ob.base.data(), sizeof(int32_t) * ob.base.size(), cudaMemcpyHostToDevice));
+    if (!ob.oct.empty()) {
+      CU_TRY(cudaMalloc((void **)&g->d_oct, sizeof(int32_t) * ob.oct.size()));
+      CU_TRY(cudaMemcpy(g->d_oct, ob.oct.data(), sizeof(int32_t) * ob.oct.size(), cudaMemcpyHostToDevice));
+    }
+    CU_TRY(cudaMalloc((void **)&g->d_binfo, sizeof(int4) * bi.size()));
+    CU_TRY(cudaMemcpy(g->d_binfo, bi.data(), sizeof(int4) * bi.size(), cudaMemcpyHostToDevice));
+    v.base = g->d_base;
+    v.oct = g->d_oct;
+    v.binfo = g->d_binfo;
   }
   return AIR_OK;
 }

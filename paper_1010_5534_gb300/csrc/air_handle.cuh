@@ -145,8 +145,7 @@ struct air_grid {
   cudaStream_t stream = nullptr;
   air::GridView gv{};
   // owned device memory
-  float *d_rho = nullptr;
-  uint32_t *d_xq = nullptr;
+  void *d_cells = nullptr;
   int32_t *d_base = nullptr, *d_oct = nullptr;
   int4 *d_binfo = nullptr;
   float *d_table = nullptr, *d_kappa = nullptr, *d_invkappa = nullptr;

@@ -11,6 +11,7 @@ namespace air {
 constexpr int kMaxBands = 64;
 constexpr int kMaxLevels = 16;
 constexpr int kXqFracBits = 24;  // table coordinate fixed point: 8 integer, 24 fraction bits
+enum { kCellRho = 0, kCellLam = 1, kCellXq = 2 };
 
 // Grid as the kernels see it. Positions are in units of the finest cell
 // (uniform: the cell), F = (x - lo) / h per axis.
@@ -18,10 +19,14 @@ struct GridView {
   int kind;             // AIR_GRID_UNIFORM / AIR_GRID_AMR
   int nf[3];            // finest cells per axis
   double lo[3], h[3];   // world origin and finest cell size
-  // cell fields: rho (float) and, for emis_mode 1, the fixed-point table
-  // coordinate of T: xq = round(x * 2^24), x = (log10 T - logT_lo) / dlogT in bins
-  const float *rho;
-  const uint32_t *xq;
+  // cell fields, one record per cell (cell_fmt):
+  //   kCellRho  : float rho                                 (emission j = rho^2)
+  //   kCellLam  : float2 {rho, Lambda(T)}                   (one band, Lambda
+  //               interpolated once per cell at upload, in FP64)
+  //   kCellXq   : uint2 {rho bits, xq}, xq = round(x 2^24) the fixed-point
+  //               table coordinate of T, x = (log10 T - logT_lo) / dlogT in bins
+  const void *cells;
+  int cell_fmt;
   // block AMR
   int B, log2B, Lm;     // brick edge (cells), log2 of it, finest level
   int nb0[3];           // level-0 bricks per axis

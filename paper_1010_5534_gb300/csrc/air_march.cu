@@ -22,8 +22,8 @@ __global__ void __launch_bounds__(kMarchBlock, MinBlocks<NBT>::value)
   bc.tab = smem;
   bc.tstride = tstride;
   bc.nbh = nbh;
-  bc.emis = g.emis_mode;
-  if (g.emis_mode)
+  bc.fmt = g.cell_fmt;
+  if (g.cell_fmt == kCellXq)
     for (int x = threadIdx.x; x < nbh * tstride; x += blockDim.x) smem[x] = g.table[b0 * tstride + x];
   BandRegs<NBT> br;
 #pragma unroll

@@ -41,7 +41,8 @@ struct RTState {
 
 struct BandCtx {
   const float *tab;  // shared: [NBT][tstride]
-  int tstride, nbh, emis;
+  int tstride, nbh;
+  int fmt;           // cell format (kCellRho / kCellLam / kCellXq)
 };
 
 // Per-band constants held in registers for the whole ray.
@@ -67,24 +68,27 @@ __device__ __forceinline__ void rt_init(RTState<NBT> &r) {
   }
 }
 
-// One cell chord of length ds with density rho and table coordinate xq.
+// One cell chord of length ds: density rho, and aux = Lambda (kCellLam, as
+// float bits) or the table coordinate of T (kCellXq).
 template <int NBT>
-__device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t xq, float ds,
+__device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t aux, float ds,
                                         const BandCtx &bc, const BandRegs<NBT> &br) {
   kahan_add(r.N, r.cN, rho * ds);
   r.steps += 1;
   int k = 0;
-  float w = 0.f;
-  if (bc.emis) {
-    k = (int)(xq >> kXqFracBits);
-    w = (float)(xq & ((1u << kXqFracBits) - 1u)) * (1.0f / (float)(1u << kXqFracBits));
+  float w = 0.f, lam1 = 1.f;
+  if (bc.fmt == kCellXq) {
+    k = (int)(aux >> kXqFracBits);
+    w = (float)(aux & ((1u << kXqFracBits) - 1u)) * (1.0f / (float)(1u << kXqFracBits));
+  } else if (bc.fmt == kCellLam) {
+    lam1 = __uint_as_float(aux);
   }
   const float rho2ds = rho * rho * ds;
 #pragma unroll
   for (int b = 0; b < NBT; ++b) {
     if (b < bc.nbh) {
-      float lam = 1.f;
-      if (bc.emis) {
+      float lam = lam1;
+      if (bc.fmt == kCellXq) {
         const float *t = bc.tab + b * bc.tstride + k;
         lam = fmaf(w, t[1] - t[0], t[0]);
       }
@@ -107,10 +111,24 @@ __device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t xq,
   }
 }
 
+// Fields of cell idx: rho and the auxiliary word of the format.
+template <typename Idx>
+__device__ __forceinline__ void load_cell(const void *__restrict__ cells, int fmt, Idx idx,
+                                          float &rho, uint32_t &aux) {
+  if (fmt == kCellRho) {
+    rho = __ldg((const float *)cells + idx);
+    aux = 0u;
+  } else {
+    const uint2 c = __ldg((const uint2 *)cells + idx);
+    rho = __uint_as_float(c.x);
+    aux = c.y;
+  }
+}
+
 // DDA through a block of nx x ny x nz cells, entered in cell (lx, ly, lz).
 // Q: entry point relative to the low corner of the entry cell (in cells),
 // Dl: direction (cells per unit t), tend: block exit relative to the entry.
-// rho / xq point at the block's cell (0, 0, 0); cell (x, y, z) is at
+// cells points at the block's cell (0, 0, 0); cell (x, y, z) is record
 // z*sz + y*sy + x. Boundary parameters are measured from the entry cell, so
 // their FP32 rounding grows with the distance marched inside the block, not
 // with the ray's distance from the origin. The fields of the next cell are
@@ -119,9 +137,8 @@ __device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t xq,
 template <int NBT, typename Idx>
 __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], const float Dl[3],
                                             float tend, int lx, int ly, int lz, int nx, int ny,
-                                            int nz, Idx sy, Idx sz, const float *__restrict__ rho,
-                                            const uint32_t *__restrict__ xq, const BandCtx &bc,
-                                            const BandRegs<NBT> &br) {
+                                            int nz, Idx sy, Idx sz, const void *__restrict__ cells,
+                                            const BandCtx &bc, const BandRegs<NBT> &br) {
   const float INF = FLT_MAX;
   const int s0 = Dl[0] > 0.f ? 1 : -1, s1 = Dl[1] > 0.f ? 1 : -1, s2 = Dl[2] > 0.f ? 1 : -1;
   const int p0 = Dl[0] > 0.f, p1 = Dl[1] > 0.f, p2 = Dl[2] > 0.f;
@@ -134,8 +151,9 @@ __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], c
   float tm1 = Dl[1] != 0.f ? ((float)p1 - Q[1]) * i1 : INF;
   float tm2 = Dl[2] != 0.f ? ((float)p2 - Q[2]) * i2 : INF;
   Idx idx = (Idx)lz * sz + (Idx)ly * sy + (Idx)lx;
-  float rh = __ldg(rho + idx);
-  uint32_t xv = bc.emis ? __ldg(xq + idx) : 0u;
+  float rh;
+  uint32_t xv;
+  load_cell(cells, bc.fmt, idx, rh, xv);
   float tl = 0.f;
   for (;;) {
     const float tn = fminf(fminf(tm0, tm1), fminf(tm2, tend));
@@ -160,10 +178,7 @@ __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], c
         idx += d2;
         tm2 = ((float)(r2 + p2) - Q[2]) * i2;
       }
-      if (more) {
-        rh_n = __ldg(rho + idx);
-        if (bc.emis) xv_n = __ldg(xq + idx);
-      }
+      if (more) load_cell(cells, bc.fmt, idx, rh_n, xv_n);
     }
     if (ds > 0.f) rt_cell<NBT>(r, rh, xv, ds, bc, br);
     if (!more) break;  // left the block (through its far face, or by rounding)
@@ -232,7 +247,7 @@ __device__ void march_uniform(RTState<NBT> &r, const GridView &g, const double O
   }
   // the ray leaves through a face of the grid: no end parameter needed
   march_block<NBT, int64_t>(r, Q, Dl, FLT_MAX, lc[0], lc[1], lc[2], g.nf[0], g.nf[1], g.nf[2],
-                            (int64_t)g.nf[0], (int64_t)g.nf[0] * g.nf[1], g.rho, g.xq, bc, br);
+                            (int64_t)g.nf[0], (int64_t)g.nf[0] * g.nf[1], g.cells, bc, br);
 }
 
 // Double-float helpers (error-free transformations: Knuth's TwoSum and the
@@ -354,8 +369,9 @@ __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
       if (tend < 0.f) tend = 0.f;
     }
     const int64_t boff = (int64_t)code << (3 * lb);
-    march_block<NBT, int>(r, Q, Dl, tend, lc[0], lc[1], lc[2], B, B, B, B, B * B, g.rho + boff,
-                          g.xq ? g.xq + boff : nullptr, bc, br);
+    const void *cb = g.cell_fmt == kCellRho ? (const void *)((const float *)g.cells + boff)
+                                            : (const void *)((const uint2 *)g.cells + boff);
+    march_block<NBT, int>(r, Q, Dl, tend, lc[0], lc[1], lc[2], B, B, B, B, B * B, cb, bc, br);
     if (ax < 0) break;
     // advance to the exit point
     if (deep) t = f2_from(te);
