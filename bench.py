@@ -200,6 +200,51 @@ def run_batch(args):
                       "per_view_rays_and_steps_equal_to_sequential": same}), flush=True)
 
 
+def run_ring(args):
+    """The paper's test calculation (Section 3, Table 1) on GB300: fixed 512^2
+    against AIR (32^2 base, 4 levels) at xi_crit 0.2, 0.5, 0.8; pixel counts,
+    flux errors against the grid-summed flux, image times."""
+    import torch
+    import paper_1010_5534_gb300 as air
+    air.build()
+    sc = scenes.ring_amr()
+    g = air.Grid(sc)
+    v = scenes.ring_view()
+    st = torch.cuda.current_stream()
+    tab = sc.lambda_table[0].astype(np.float64)
+    nt = tab.size
+    hf = (sc.hi[0] - sc.lo[0]) / 512
+    ex = 0.0
+    for b in range(len(sc.brick_level)):
+        T = sc.temp[b].astype(np.float64)
+        x = np.clip((np.log10(T) - sc.logT_lo) / (sc.logT_hi - sc.logT_lo) * (nt - 1), 0, nt - 1)
+        k = np.minimum(np.floor(x).astype(int), nt - 2)
+        lam = (1 - (x - k)) * tab[k] + (x - k) * tab[k + 1]
+        ex += (sc.rho[b].astype(np.float64) ** 2 * lam).sum() * (hf * (1 << (4 - sc.brick_level[b]))) ** 3
+    rows = []
+    for _ in range(args.warmup):
+        g.render_fixed(v, 512, fields=("band_flux",))
+    ms_f = min(_timed(lambda: g.render_fixed(v, 512, fields=("band_flux",)), st)[0]
+               for _ in range(max(args.steps, 1)))
+    f = g.render_fixed(v, 512, fields=("band_flux",))
+    rows.append(dict(calc="fixed 512^2", pixels=512 * 512, ms=ms_f,
+                     flux_err=(ex - float(f["band_flux"][0])) / ex))
+    for xc in (0.2, 0.5, 0.8):
+        for _ in range(args.warmup):
+            g.render_adaptive(v, 32, 4, xc, fields=("band_flux",))
+        ms = min(_timed(lambda: g.render_adaptive(v, 32, 4, xc, fields=("band_flux",)), st)[0]
+                 for _ in range(max(args.steps, 1)))
+        r = g.render_adaptive(v, 32, 4, xc, fields=("band_flux",))
+        rows.append(dict(calc=f"AIR xi_crit {xc}", pixels=int(r["n_rays"]), ms=ms,
+                         flux_err=(ex - float(r["band_flux"][0])) / ex,
+                         speedup_vs_fixed=ms_f / ms, pixel_saving=512 * 512 / r["n_rays"]))
+    print(json.dumps({"workload": "Section 3 ring (Eq. 3) on 4^3 blocks of 8^3 cells, 4 levels "
+                                  "(512^3 effective), face-on; Table 1 calculations",
+                      "table": rows, "paper_table1_pixels": {"fixed": 262144, "0.2": 40512,
+                                                             "0.5": 23384, "0.8": 22748}}),
+          flush=True)
+
+
 def run_learned(args):
     """Learned depth proposal: plain AIR trees of seed-varied cone grids (the
     clumping redrawn per seed) at random views give (features, depth) samples;
@@ -288,7 +333,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="air", choices=["air", "batch", "learned"],
+    ap.add_argument("--workload", default="air", choices=["air", "batch", "learned", "ring"],
                     help="air: the benchmark line (one adaptive image of the cone grid); "
                          "batch: 64 views x 16 bands in one persistent launch vs one by one; "
                          "learned: train the depth network on 2000 plain trees, evaluate")
@@ -304,6 +349,8 @@ def main():
         return run_batch(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "ring":
+        return run_ring(args)
     assert args.warmup >= 3 or args.profile_case, "at least 3 warm-up steps"
 
     import torch

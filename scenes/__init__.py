@@ -413,3 +413,97 @@ def refine_uniform_to_amr(scene: Scene, brick: int, refine_mask_fn, seed: int = 
                  brick_level=np.array(levels, np.int32),
                  brick_origin=np.array(origins, np.int32), emis_mode=0, kappa=scene.kappa,
                  name=scene.name + "_amr2")
+
+
+# --------------------------------------------------------------------------
+# The paper's test problem (Section 3, Eq. 3): a hot ring on a block-AMR grid
+# --------------------------------------------------------------------------
+RING_LENGTH_UNIT_CM = 1e17
+RING_DENSITY_UNIT = 1e-26  # g cm^-3
+
+
+def _ring_boundary_distance(x, r, half_w, r_in, r_out):
+    """Distance from points (|x|, r) to the boundary of the ring's cross-section
+    rectangle [-half_w, half_w] x [r_in, r_out] in the (x, r) half-plane."""
+    ax = np.abs(x)
+    inside = (ax <= half_w) & (r >= r_in) & (r <= r_out)
+    dx_out = np.maximum(ax - half_w, 0.0)
+    dr_out = np.maximum(np.maximum(r_in - r, r - r_out), 0.0)
+    d_out = np.hypot(dx_out, dr_out)
+    d_in = np.minimum(np.minimum(half_w - ax, r - r_in), r_out - r)
+    return np.where(inside, d_in, d_out), inside
+
+
+def ring_amr(n_base: int = 32, brick: int = 8, levels: int = 4, beta_g_per_cm: float = 2.5e9,
+             rho_out_gcc: float = 1e-25, T_in: float = 1e8, T_out: float = 1e4,
+             e_lo: float = 1.0, e_hi: float = 10.0, n_tbins: int = 64) -> Scene:
+    """Section 3's test problem on a PARAMESH-like grid: a ring in the yz-plane
+    (thickness 1e17 cm, |x| < w/2; inner and outer radii 3.5e17 and 4e17 cm) in
+    a box of +-5e17 cm; rho = beta r_yz^-2 in the ring (Eq. 3) and 1e-25 g cm^-3
+    elsewhere; T = 1e8 K in the ring, 1e4 K elsewhere. 4^3 base bricks of 8^3
+    cells, 4 nested levels (512^3 effective) on bricks the ring's surface passes
+    through, as a density/temperature refinement would place them. Emission in
+    the 1-10 keV band from the bremsstrahlung-shaped table; optically thin.
+
+    Units: lengths in 1e17 cm, density in 1e-26 g cm^-3 (so FP32 rho^2 stays
+    normal). beta = 2.5e9 g cm^-1 (the printed 2.5e-9 would make the ring 1e19
+    times less dense than its surroundings and its flux ~1e-55 instead of the
+    quoted 1.4e-19 erg s^-1 cm^-2)."""
+    L = RING_LENGTH_UNIT_CM
+    half_w, r_in, r_out = 0.5e17 / L, 3.5e17 / L, 4e17 / L
+    lo, hi = -5e17 / L, 5e17 / L
+    nf = n_base << levels
+    hf = (hi - lo) / nf
+    nb0 = n_base // brick
+    g = np.arange(nb0)
+    bz, by, bx = np.meshgrid(g, g, g, indexing="ij")
+    S0 = brick << levels
+    cur = np.stack([bx.ravel(), by.ravel(), bz.ravel()], axis=1).astype(np.int64) * S0
+    leaf_levels, leaf_origins = [], []
+    for lev in range(levels + 1):
+        S = brick << (levels - lev)
+        ctr = lo + (cur + S / 2.0) * hf
+        rr = np.hypot(ctr[:, 1], ctr[:, 2])
+        d, _ = _ring_boundary_distance(ctr[:, 0], rr, half_w, r_in, r_out)
+        refine = (d <= math.sqrt(3.0) * 0.5 * S * hf) if lev < levels else np.zeros(len(cur), bool)
+        leaf_levels.append(np.full(int((~refine).sum()), lev, dtype=np.int32))
+        leaf_origins.append(cur[~refine])
+        ref = cur[refine]
+        h = S // 2
+        kids = [ref + np.array([dx * h, dy * h, dz * h]) for dz in (0, 1) for dy in (0, 1) for dx in (0, 1)]
+        cur = np.concatenate(kids) if len(ref) else np.zeros((0, 3), np.int64)
+    levels_arr = np.concatenate(leaf_levels)
+    origins = np.concatenate(leaf_origins, axis=0)
+    nb = len(levels_arr)
+    off = np.arange(brick) + 0.5
+    rho = np.empty((nb, brick, brick, brick), np.float32)
+    temp = np.empty((nb, brick, brick, brick), np.float32)
+    for lev in range(levels + 1):
+        sel = np.nonzero(levels_arr == lev)[0]
+        if not len(sel):
+            continue
+        step = 1 << (levels - lev)
+        o = origins[sel].astype(np.float64)
+        cx = lo + (o[:, 0:1] + off[None, :] * step) * hf
+        cy = lo + (o[:, 1:2] + off[None, :] * step) * hf
+        cz = lo + (o[:, 2:3] + off[None, :] * step) * hf
+        shp = (len(sel), brick, brick, brick)
+        PX = np.broadcast_to(cx[:, None, None, :], shp)
+        PY = np.broadcast_to(cy[:, None, :, None], shp)
+        PZ = np.broadcast_to(cz[:, :, None, None], shp)
+        r = np.hypot(PY, PZ)
+        inside = (np.abs(PX) < half_w) & (r >= r_in) & (r <= r_out)
+        rho_in = beta_g_per_cm / (r * L) ** 2 / RING_DENSITY_UNIT
+        rho[sel] = np.where(inside, rho_in, rho_out_gcc / RING_DENSITY_UNIT).astype(np.float32)
+        temp[sel] = np.where(inside, T_in, T_out).astype(np.float32)
+    edges = band_edges(1, e_lo, e_hi)
+    return Scene(kind="amr", lo=(lo,) * 3, hi=(hi,) * 3, n=(n_base,) * 3, rho=rho, temp=temp,
+                 brick=brick, max_level=levels, brick_level=levels_arr,
+                 brick_origin=origins.astype(np.int32), emis_mode=1,
+                 lambda_table=cooling_table(edges, n_tbins), logT_lo=4.0, logT_hi=9.0,
+                 kappa=np.zeros(1), name=f"ring_{n_base}^3_b{brick}_L{levels}")
+
+
+def ring_view() -> View:
+    """Face-on view along +x with (u, v) = (y, z) (the paper's Fig. 1)."""
+    return View(dir=(1.0, 0.0, 0.0), up=(0.0, 0.0, 1.0), half_extent=5e17 / RING_LENGTH_UNIT_CM)

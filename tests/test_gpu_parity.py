@@ -127,6 +127,23 @@ def test_fixed_res_one_and_face_aligned(wind):
         close(np_(r["intensity"])[0], f["inten"][:, 0], f"I res {res}")
 
 
+def test_face_aligned_rays_with_inexact_reciprocal_cell_size():
+    """Box of width 10 with 32 cells: h = 5/16 is exact but 1/h = 3.2 is not.
+    Pixel centres of a 16^2 image lie exactly on cell faces; the half-open rule
+    must pick the higher cell exactly as the oracle's division does."""
+    rng = np.random.default_rng(5)
+    rho = np.exp(rng.normal(size=(32, 32, 32)))
+    sc = scenes.uniform_from_array(rho, lo=(-5.0,) * 3, hi=(5.0,) * 3, kappa=0.05)
+    g, o = air.Grid(sc), oracle.Oracle(sc)
+    for axis in ("+x", "-y", "+z"):
+        v = scenes.axis_view(axis, half_extent=5.0)
+        for res in (16, 8):
+            r, f = fixed_pair(sc, g, o, v, res)
+            close(np_(r["coldens"]), f["col"], f"N {axis} {res}")
+            close(np_(r["intensity"])[0], f["inten"][:, 0], f"I {axis} {res}")
+            assert r["n_steps"] == int(f["steps"].sum())
+
+
 # ------------------------------------------------------------------ adaptive images
 def nodes_of(r):
     return {k: np_(r[k]) for k in ("level", "i", "j", "is_leaf", "coldens", "p")} | \
