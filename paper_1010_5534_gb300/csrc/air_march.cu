@@ -5,7 +5,7 @@ namespace air {
 
 template <int NBT>
 struct MinBlocks {
-  static constexpr int value = NBT <= 1 ? 6 : (NBT <= 2 ? 5 : (NBT <= 4 ? 4 : (NBT <= 8 ? 3 : 2)));
+  static constexpr int value = NBT <= 1 ? 8 : (NBT <= 2 ? 5 : (NBT <= 4 ? 4 : (NBT <= 8 ? 3 : 2)));
 };
 
 constexpr int kMarchBlock = 128;
