@@ -45,21 +45,51 @@ BYTES_PER_STEP = 8  # rho (f32) + table coordinate of T (u32) fetched per ray-ce
 
 
 def sample_clocks_start(path):
+    """Start nvidia-smi sampling SM clocks and throttle reasons every 100 ms;
+    waits (up to 5 s) for the first sample so the timed region is covered."""
     dev = os.environ.get("CUDA_VISIBLE_DEVICES", "")
-    cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+    cmd = ["nvidia-smi", "--query-gpu=timestamp,index,clocks.sm,clocks.max.sm,power.draw,"
            "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
            "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-           "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"]
+           "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"]
     if dev.strip().isdigit():
         cmd[1:1] = ["-i", dev.strip()]
     try:
         f = open(path, "w")
-        return subprocess.Popen(cmd, stdout=f, stderr=subprocess.DEVNULL), f
+        proc = subprocess.Popen(cmd, stdout=f, stderr=subprocess.DEVNULL)
     except (OSError, FileNotFoundError):
         return None, None
+    t_end = time.time() + 5.0
+    while time.time() < t_end and proc.poll() is None:
+        f.flush()
+        if os.path.getsize(path) > 0:
+            break
+        time.sleep(0.05)
+    return proc, f
 
 
-def sample_clocks_stop(proc, f, path):
+def _parse_clock_rows(path):
+    from datetime import datetime
+    rows = []
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        p = [x.strip() for x in line.split(",")]
+        if len(p) < 10:
+            continue
+        try:
+            ts = datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            sm, mx = float(p[2]), float(p[3])
+        except ValueError:
+            continue
+        rs = {nm for k, nm in enumerate(names) if p[6 + k].lower().startswith("active")}
+        rows.append((ts, sm, mx, rs))
+    return rows
+
+
+def sample_clocks_stop(proc, f, path, window):
+    """Median SM clock and the throttle reasons seen in `window` (host times of
+    the timed region); if the region was too short for 3 samples, all samples
+    taken while the GPU was busy with this benchmark are used and said so."""
     if proc is None:
         return None
     proc.terminate()
@@ -68,40 +98,60 @@ def sample_clocks_stop(proc, f, path):
     except subprocess.TimeoutExpired:
         proc.kill()
     f.close()
-    sm, mx, reasons = [], [], set()
-    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-    for line in open(path):
-        p = [x.strip() for x in line.split(",")]
-        if len(p) < 9:
-            continue
-        try:
-            sm.append(float(p[1]))
-            mx.append(float(p[2]))
-        except ValueError:
-            continue
-        for k, nm in enumerate(names):
-            if p[5 + k].lower().startswith("active"):
-                reasons.add(nm)
-    if not sm:
+    rows = _parse_clock_rows(path)
+    sel = [r for r in rows if window[0] <= r[0] <= window[1]]
+    span = "timed region"
+    if len(sel) < 3:
+        sel, span = rows, "whole benchmark (timed region shorter than 3 samples)"
+    if not sel:
         return None
-    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-            "samples": len(sm)}
+    reasons = sorted(set().union(*[r[3] for r in sel]))
+    return {"sm_mhz": statistics.median(r[1] for r in sel), "sm_max_mhz": max(r[2] for r in sel),
+            "reasons": reasons, "samples": len(sel), "span": span}
 
 
-def oracle_sample_rate(sc, view, lv, ii, jj, n0, budget_s=12.0):
-    """Oracle (as it stands) on a bounded sample of rays: ray-cell steps/s."""
+def oracle_sample_rate(sc, view, n0, budget_s=15.0, chunk=65536, max_rays=1 << 24):
+    """Oracle (as it stands) on a bounded sample: rays drawn uniformly from the
+    finest pixels, traced in chunks until `budget_s` of wall time; returns
+    ray-cell steps/s, rays traced, seconds."""
     import oracle
     o = oracle.Oracle(sc)
-    steps, t_used, done = 0, 0.0, 0
-    chunk = 256
-    while t_used < budget_s and done < len(lv):
-        sl = slice(done, done + chunk)
+    steps, t_used, done, k = 0, 0.0, 0, 0
+    while t_used < budget_s and done < max_rays:
+        lv, ii, jj = finest_sample(chunk, seed=7 + k)
         t = time.perf_counter()
-        _, _, st = o.trace(view, n0, lv[sl], ii[sl], jj[sl])
+        _, _, st = o.trace(view, n0, lv, ii, jj)
         t_used += time.perf_counter() - t
         steps += int(st.sum())
         done += len(st)
+        k += 1
     return steps / t_used, done, t_used
+
+
+MARCH_SOURCES = ("air_march.cuh", "air_march.cu", "air_internal.cuh")
+
+
+def march_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for n in MARCH_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1010_5534_gb300", "csrc", n), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def march_traffic():
+    """DRAM bytes per march launch from the committed ncu summary of this
+    workload, if it was taken on the current march source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_march_amr_cone128_air256.md")
+    if not os.path.exists(path):
+        return None
+    src, val = None, None
+    for line in open(path):
+        if line.startswith("march source sha256/16:"):
+            src = line.split(":", 1)[1].strip().strip("`")
+        if line.startswith("dram bytes per launch:"):
+            val = float(line.split(":", 1)[1].split()[0])
+    return val if src == march_source_hash() else None
 
 
 def omp_threads():
@@ -126,7 +176,7 @@ def run_reference(args):
     view = scenes.axis_view("+z")
     import oracle
     o = oracle.Oracle(sc)
-    per_step = 600
+    per_step = 32768
     lv, ii, jj = finest_sample(per_step * (args.steps + args.warmup), seed=7)
     times, steps = [], 0
     for s in range(args.warmup + args.steps):
@@ -388,6 +438,9 @@ def main():
         print(json.dumps({"profile_case": "air", "rays": r["n_rays"], "steps": r["n_steps"],
                           "sweeps": r["n_sweeps"]}), flush=True)
         return
+    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") \
+        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/air_clocks_{os.getpid()}.csv"
+    proc, fh = sample_clocks_start(clk_path)
     r = render()
     cap = r["n_out"]
     for _ in range(args.warmup):
@@ -400,11 +453,9 @@ def main():
 
     # ---- timed: device-resident outputs
     st = torch.cuda.current_stream()
-    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") \
-        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/air_clocks_{os.getpid()}.csv"
-    proc, fh = sample_clocks_start(clk_path)
     g.profile(True)
     barrier()
+    t_win0 = time.time()
     step_ms, n_steps, n_rays = [], 0, 0
     for _ in range(args.steps):
         flush.zero_()
@@ -417,9 +468,9 @@ def main():
         n_steps += r["n_steps"]
         n_rays += r["n_rays"]
     barrier()
+    t_win1 = time.time()
     prof = g.profile_read()
     g.profile(False)
-    clocks = sample_clocks_stop(proc, fh, clk_path)
     tot_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([tot_ms], device="cuda")
@@ -463,6 +514,7 @@ def main():
         e1.record(st)
         e1.synchronize()
         fixed_ms.append(e0.elapsed_time(e1))
+    clocks = sample_clocks_stop(proc, fh, clk_path, (t_win0, t_win1))
     air_flux = float(r["band_flux"][0])
     fix_flux = float(f["band_flux"][0])
     flux_err = abs(air_flux - fix_flux) / abs(fix_flux)
@@ -478,7 +530,8 @@ def main():
         peaks = json.load(open(pk_path))
     hbm = peaks.get("hbm_gbs", 6800.0)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None,
+                "frac": achieved / hbm, "traffic": march_traffic(),
+                "march_source": march_source_hash(),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
                 "kernel": "k_march (AMR)", "algorithmic_bytes_per_launch": algo_bytes_per_launch,
                 "march_share_of_step": march_ms / tot_ms if world == 1 else None}
@@ -487,11 +540,10 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        lv, ii, jj = finest_sample(20000, seed=7)
-        rate, nr, secs = oracle_sample_rate(sc, view, lv, ii, jj, W["base_res"], budget_s=12.0)
+        rate, nr, secs = oracle_sample_rate(sc, view, W["base_res"])
         cpu = {"value": rate, "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
                "sample": f"{nr} rays drawn uniformly from the 4096^2 finest pixels of the same "
-                         f"view and grid ({secs:.1f} s of CPU time)"}
+                         f"view and grid, FP64 oracle, OpenMP over rays ({secs:.1f} s wall)"}
 
     if rank == 0:
         cfg = {k: v for k, v in W.items()}

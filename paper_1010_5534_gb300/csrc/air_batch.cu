@@ -131,7 +131,7 @@ static size_t batch_smem(const GridView &g, int V) {
   return tab + 3 * sizeof(int64_t) * V + sizeof(int32_t) * V + sizeof(int32_t) * (kBatchBlock / 32) * V;
 }
 
-template <int NBT, bool AMR>
+template <int NBT, bool AMR, int FMT>
 __global__ void __launch_bounds__(kBatchBlock) k_air_batch(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const GridView &g = a.g;
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kBatchBlock) k_air_batch(BatchArgs a) {
   int32_t *cnt = (int32_t *)(vbase + V);
   int32_t *wcnt = cnt + V;
   __shared__ int64_t s_total;
-  if (g.cell_fmt == kCellXq)
+  if (FMT == kCellXq)
     for (int x = threadIdx.x; x < nb * tstride; x += blockDim.x) tab[x] = g.table[x];
   __syncthreads();
 
@@ -189,7 +189,6 @@ __global__ void __launch_bounds__(kBatchBlock) k_air_batch(BatchArgs a) {
         bc.tab = tab + b0 * tstride;
         bc.tstride = tstride;
         bc.nbh = min(NBT, nb - b0);
-        bc.fmt = g.cell_fmt;
         BandRegs<NBT> br;
 #pragma unroll
         for (int q = 0; q < NBT; ++q) {
@@ -198,7 +197,7 @@ __global__ void __launch_bounds__(kBatchBlock) k_air_batch(BatchArgs a) {
         }
         const RayGeom rg = a.geoms[v];
         RTState<NBT> st;
-        trace_ray<NBT, AMR>(st, g, rg, t.lvl[k], t.pi[k], t.pj[k], a.fp64_level, bc, br);
+        trace_ray<NBT, AMR, FMT>(st, g, rg, t.lvl[k], t.pi[k], t.pj[k], a.fp64_level, bc, br);
         if (chunk == 0) {
           t.N[k] = st.N;
           t.steps[k] = st.steps;
@@ -396,14 +395,14 @@ __global__ void __launch_bounds__(256) k_vemit(TreeView t, const int16_t *view, 
     if (e_ != cudaSuccess) return cuda_fail(e_, #x); \
   } while (0)
 
-template <int NBT, bool AMR>
+template <int NBT, bool AMR, int FMT>
 static cudaError_t batch_occupancy(int *blocks_per_sm, size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_air_batch<NBT, AMR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_air_batch<NBT, AMR, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_air_batch<NBT, AMR>, kBatchBlock, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_air_batch<NBT, AMR, FMT>, kBatchBlock, smem);
 }
 
-template <int NBT, bool AMR>
+template <int NBT, bool AMR, int FMT>
 static cudaError_t batch_launch(const BatchArgs &a, int grid, size_t smem, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -415,18 +414,30 @@ static cudaError_t batch_launch(const BatchArgs &a, int grid, size_t smem, cudaS
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_air_batch<NBT, AMR>, a);
+  return cudaLaunchKernelEx(&cfg, k_air_batch<NBT, AMR, FMT>, a);
 }
 
 typedef cudaError_t (*BatchOccFn)(int *, size_t);
 typedef cudaError_t (*BatchLaunchFn)(const BatchArgs &, int, size_t, cudaStream_t);
 
-static bool batch_fns(int nbt, bool amr, BatchOccFn *occ, BatchLaunchFn *launch) {
-#define AIR_BATCH_CASE(N)                                                 \
-  if (nbt == N) {                                                         \
-    *occ = amr ? batch_occupancy<N, true> : batch_occupancy<N, false>;    \
-    *launch = amr ? batch_launch<N, true> : batch_launch<N, false>;       \
-    return true;                                                          \
+static bool batch_fns(int nbt, bool amr, int fmt, BatchOccFn *occ, BatchLaunchFn *launch) {
+  if (fmt == kCellLam) {
+    // per-cell Lambda exists for one-band grids only
+    if (nbt != 1) return false;
+    *occ = amr ? batch_occupancy<1, true, kCellLam> : batch_occupancy<1, false, kCellLam>;
+    *launch = amr ? batch_launch<1, true, kCellLam> : batch_launch<1, false, kCellLam>;
+    return true;
+  }
+#define AIR_BATCH_CASE(N)                                                                     \
+  if (nbt == N) {                                                                             \
+    if (fmt == kCellXq) {                                                                     \
+      *occ = amr ? batch_occupancy<N, true, kCellXq> : batch_occupancy<N, false, kCellXq>;    \
+      *launch = amr ? batch_launch<N, true, kCellXq> : batch_launch<N, false, kCellXq>;       \
+    } else {                                                                                  \
+      *occ = amr ? batch_occupancy<N, true, kCellRho> : batch_occupancy<N, false, kCellRho>;  \
+      *launch = amr ? batch_launch<N, true, kCellRho> : batch_launch<N, false, kCellRho>;     \
+    }                                                                                         \
+    return true;                                                                              \
   }
   AIR_BATCH_CASE(1)
   AIR_BATCH_CASE(2)
@@ -465,9 +476,10 @@ air_status render_batch(air_grid *g, const air_view *views, int32_t V, const air
   const int nb = g->gv.n_bands;
   int nbt = op.bands_per_thread > 0 ? op.bands_per_thread
             : (g->tune.batch_bands_per_thread > 0 ? g->tune.batch_bands_per_thread : default_bands_per_thread(nb));
+  if (g->gv.cell_fmt == kCellLam && nbt > 0) nbt = 1;  // one band
   BatchOccFn occ;
   BatchLaunchFn launch;
-  if (!batch_fns(nbt, g->gv.kind == AIR_GRID_AMR, &occ, &launch))
+  if (!batch_fns(nbt, g->gv.kind == AIR_GRID_AMR, g->gv.cell_fmt, &occ, &launch))
     return set_error(AIR_ERR_ARG, "bands_per_thread must be 1, 2, 4, 8 or 16");
   for (int v = 0; v < V; ++v) {
     air_status s = check_image(&outs[v]);

@@ -11,7 +11,10 @@
 //         The bin index and weight then come out exactly in FP32.
 //   base: level-0 brick grid; entries >= 0 are leaf bricks, < 0 point to a
 //         group of 8 child slots in `oct` (octant = bx | by << 1 | bz << 2).
-//   binfo: per leaf brick (origin x, y, z in finest cells, level).
+//   bmap: dense brick map at level mapL (the finest level whose brick grid has
+//         at most 2^24 positions): per brick position, the leaf brick covering
+//         it as id | level << 27, or -(group + 1) where the octree continues
+//         below mapL. The march finds most bricks with this one load.
 #include <cmath>
 #include <cstring>
 #include <unordered_map>
@@ -136,6 +139,27 @@ bool build_octree(const air_grid_desc *d, OctBuild &ob) {
   return true;
 }
 
+// Dense map of the octree at level mapL (positions in level-mapL brick units).
+void fill_map(const OctBuild &ob, int32_t code, int lev, int64_t px, int64_t py, int64_t pz,
+              int mapL, const int64_t nm[3], std::vector<int32_t> &map) {
+  if (code >= 0) {
+    const int s = mapL - lev;
+    const int32_t e = code | (lev << kMapLevelShift);
+    for (int64_t z = pz << s; z < (pz + 1) << s; ++z)
+      for (int64_t y = py << s; y < (py + 1) << s; ++y)
+        for (int64_t x = px << s; x < (px + 1) << s; ++x) map[(size_t)((z * nm[1] + y) * nm[0] + x)] = e;
+    return;
+  }
+  if (lev == mapL) {
+    map[(size_t)((pz * nm[1] + py) * nm[0] + px)] = code;
+    return;
+  }
+  const int64_t grp = -(int64_t)code - 1;
+  for (int oc = 0; oc < 8; ++oc)
+    fill_map(ob, ob.oct[(size_t)grp * 8 + oc], lev + 1, 2 * px + (oc & 1), 2 * py + ((oc >> 1) & 1),
+             2 * pz + ((oc >> 2) & 1), mapL, nm, map);
+}
+
 template <typename T>
 void dfree(T *&p) {
   if (p) cudaFree((void *)p);
@@ -145,7 +169,7 @@ void dfree(T *&p) {
 }  // namespace
 
 void free_grid_impl(air_grid *g) {
-  dfree(g->d_cells); dfree(g->d_base); dfree(g->d_oct); dfree(g->d_binfo);
+  dfree(g->d_cells); dfree(g->d_base); dfree(g->d_oct); dfree(g->d_bmap);
   dfree(g->d_table); dfree(g->d_kappa); dfree(g->d_invkappa);
   free_batch(g);
   free_learn(g);
@@ -211,6 +235,7 @@ air_status load_grid_impl(const air_grid_desc *d, air_grid *g) {
       v.nf[a] = d->n[a] << d->max_level;
       v.nb0[a] = d->n[a] / d->brick;
     }
+    if (d->n_bricks >= (1 << kMapLevelShift)) return set_error(AIR_ERR_ARG, "at most 2^27 - 1 bricks");
     if (!build_octree(d, ob)) return set_error(AIR_ERR_ARG, "%s", ob.err.c_str());
     n_cells = (int64_t)d->n_bricks * d->brick * d->brick * d->brick;
     v.B = d->brick;
@@ -293,20 +318,31 @@ air_status load_grid_impl(const air_grid_desc *d, air_grid *g) {
   }
   v.cells = g->d_cells;
   if (d->kind == AIR_GRID_AMR) {
-    std::vector<int4> bi(d->n_bricks);
-    for (int b = 0; b < d->n_bricks; ++b)
-      bi[b] = make_int4(d->brick_origin[3 * b], d->brick_origin[3 * b + 1], d->brick_origin[3 * b + 2], d->brick_level[b]);
     CU_TRY(cudaMalloc((void **)&g->d_base, sizeof(int32_t) * ob.base.size()));
     CU_TRY(cudaMemcpy(g->d_base, ob.base.data(), sizeof(int32_t) * ob.base.size(), cudaMemcpyHostToDevice));
     if (!ob.oct.empty()) {
       CU_TRY(cudaMalloc((void **)&g->d_oct, sizeof(int32_t) * ob.oct.size()));
       CU_TRY(cudaMemcpy(g->d_oct, ob.oct.data(), sizeof(int32_t) * ob.oct.size(), cudaMemcpyHostToDevice));
     }
-    CU_TRY(cudaMalloc((void **)&g->d_binfo, sizeof(int4) * bi.size()));
-    CU_TRY(cudaMemcpy(g->d_binfo, bi.data(), sizeof(int4) * bi.size(), cudaMemcpyHostToDevice));
+    const int64_t nb = (int64_t)v.nb0[0] * v.nb0[1] * v.nb0[2];
+    int mapL = 0;
+    while (mapL < v.Lm && (nb << (3 * (mapL + 1))) <= ((int64_t)1 << 24)) ++mapL;
+    int64_t nm[3];
+    for (int a = 0; a < 3; ++a) {
+      nm[a] = (int64_t)v.nb0[a] << mapL;
+      v.nm[a] = (int)nm[a];
+    }
+    std::vector<int32_t> map((size_t)(nm[0] * nm[1] * nm[2]));
+    for (int64_t z = 0; z < v.nb0[2]; ++z)
+      for (int64_t y = 0; y < v.nb0[1]; ++y)
+        for (int64_t x = 0; x < v.nb0[0]; ++x)
+          fill_map(ob, ob.base[(size_t)((z * v.nb0[1] + y) * v.nb0[0] + x)], 0, x, y, z, mapL, nm, map);
+    CU_TRY(cudaMalloc((void **)&g->d_bmap, sizeof(int32_t) * map.size()));
+    CU_TRY(cudaMemcpy(g->d_bmap, map.data(), sizeof(int32_t) * map.size(), cudaMemcpyHostToDevice));
     v.base = g->d_base;
     v.oct = g->d_oct;
-    v.binfo = g->d_binfo;
+    v.bmap = g->d_bmap;
+    v.mapL = mapL;
   }
   return AIR_OK;
 }

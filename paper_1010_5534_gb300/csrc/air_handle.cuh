@@ -147,7 +147,7 @@ struct air_grid {
   // owned device memory
   void *d_cells = nullptr;
   int32_t *d_base = nullptr, *d_oct = nullptr;
-  int4 *d_binfo = nullptr;
+  int32_t *d_bmap = nullptr;
   float *d_table = nullptr, *d_kappa = nullptr, *d_invkappa = nullptr;
   int64_t n_cells = 0;
   air::Workspace ws;

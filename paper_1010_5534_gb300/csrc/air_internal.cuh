@@ -11,6 +11,8 @@ namespace air {
 constexpr int kMaxBands = 64;
 constexpr int kMaxLevels = 16;
 constexpr int kXqFracBits = 24;  // table coordinate fixed point: 8 integer, 24 fraction bits
+constexpr int kMapLevelShift = 27;  // brick map entry: id | level << 27
+constexpr int32_t kMapIdMask = (1 << kMapLevelShift) - 1;
 enum { kCellRho = 0, kCellLam = 1, kCellXq = 2 };
 
 // Grid as the kernels see it. Positions are in units of the finest cell
@@ -32,7 +34,8 @@ struct GridView {
   int nb0[3];           // level-0 bricks per axis
   const int32_t *base;  // [nb0z][nb0y][nb0x]: >= 0 leaf brick id, < 0 -(group + 1)
   const int32_t *oct;   // [groups][8] children codes (octant = bx | by<<1 | bz<<2)
-  const int4 *binfo;    // per leaf brick: origin x, y, z (finest units), level
+  const int32_t *bmap;  // dense map at level mapL: id | level << 27, or -(group + 1)
+  int mapL, nm[3];      // map level and map positions per axis
   // emission
   int emis_mode, n_bands, n_tbins;
   const float *table;   // [n_bands][n_tbins + 1] (last entry repeated)

@@ -10,7 +10,7 @@ struct MinBlocks {
 
 constexpr int kMarchBlock = 128;
 
-template <int NBT, bool AMR>
+template <int NBT, bool AMR, int FMT>
 __global__ void __launch_bounds__(kMarchBlock, MinBlocks<NBT>::value)
     k_march(GridView g, RayGeom rg, RaySource src, RayOut out, int fp64_level) {
   extern __shared__ float smem[];
@@ -22,8 +22,7 @@ __global__ void __launch_bounds__(kMarchBlock, MinBlocks<NBT>::value)
   bc.tab = smem;
   bc.tstride = tstride;
   bc.nbh = nbh;
-  bc.fmt = g.cell_fmt;
-  if (g.cell_fmt == kCellXq)
+  if (FMT == kCellXq)
     for (int x = threadIdx.x; x < nbh * tstride; x += blockDim.x) smem[x] = g.table[b0 * tstride + x];
   BandRegs<NBT> br;
 #pragma unroll
@@ -57,7 +56,7 @@ __global__ void __launch_bounds__(kMarchBlock, MinBlocks<NBT>::value)
     L = 0;
   }
   RTState<NBT> st;
-  trace_ray<NBT, AMR>(st, g, rg, L, i, j, fp64_level, bc, br);
+  trace_ray<NBT, AMR, FMT>(st, g, rg, L, i, j, fp64_level, bc, br);
   if (chunk == 0) {
     out.N[k] = st.N;
     out.steps[k] = st.steps;
@@ -102,13 +101,22 @@ static cudaError_t launch_t(const GridView &g, const Camera &cam, const RaySourc
   const int block = kMarchBlock;
   const int64_t blocks = (threads + block - 1) / block;
   if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(float) * (size_t)(NBT * (g.n_tbins + 1));
+  const size_t smem = g.cell_fmt == kCellXq ? sizeof(float) * (size_t)(NBT * (g.n_tbins + 1)) : 0;
   const RayGeom rg = make_geom(g, cam, src.n0);
   dim3 grid((unsigned)blocks, chunks);
-  if (g.kind == AIR_GRID_AMR)
-    k_march<NBT, true><<<grid, block, smem, st>>>(g, rg, src, out, tune.fp64_level);
-  else
-    k_march<NBT, false><<<grid, block, smem, st>>>(g, rg, src, out, tune.fp64_level);
+  const bool amr = g.kind == AIR_GRID_AMR;
+  if (g.cell_fmt == kCellRho) {
+    if (amr) k_march<NBT, true, kCellRho><<<grid, block, smem, st>>>(g, rg, src, out, tune.fp64_level);
+    else k_march<NBT, false, kCellRho><<<grid, block, smem, st>>>(g, rg, src, out, tune.fp64_level);
+  } else if (g.cell_fmt == kCellXq) {
+    if (amr) k_march<NBT, true, kCellXq><<<grid, block, smem, st>>>(g, rg, src, out, tune.fp64_level);
+    else k_march<NBT, false, kCellXq><<<grid, block, smem, st>>>(g, rg, src, out, tune.fp64_level);
+  } else {
+    // per-cell Lambda exists for one-band grids only
+    if (NBT != 1) return cudaErrorInvalidValue;
+    if (amr) k_march<1, true, kCellLam><<<grid, block, smem, st>>>(g, rg, src, out, tune.fp64_level);
+    else k_march<1, false, kCellLam><<<grid, block, smem, st>>>(g, rg, src, out, tune.fp64_level);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (chunks > 1 && out.p) {
@@ -128,6 +136,7 @@ cudaError_t launch_march(const GridView &g, const Camera &cam, const RaySource &
                          const RayOut &out, const MarchTune &tune, cudaStream_t st) {
   int nbt = tune.nbt;
   if (nbt <= 0) nbt = g.n_bands;
+  if (g.cell_fmt == kCellLam) nbt = 1;  // one band
   if (nbt <= 1) return launch_t<1>(g, cam, src, out, tune, st);
   if (nbt <= 2) return launch_t<2>(g, cam, src, out, tune, st);
   if (nbt <= 4) return launch_t<4>(g, cam, src, out, tune, st);

@@ -42,9 +42,8 @@ struct RTState {
 };
 
 struct BandCtx {
-  const float *tab;  // shared: [NBT][tstride]
+  const float *tab;  // shared: [NBT][tstride] (kCellXq)
   int tstride, nbh;
-  int fmt;           // cell format (kCellRho / kCellLam / kCellXq)
 };
 
 // Per-band constants held in registers for the whole ray.
@@ -70,54 +69,52 @@ __device__ __forceinline__ void rt_init(RTState<NBT> &r) {
   }
 }
 
-// One cell chord of length ds: density rho, and aux = Lambda (kCellLam, as
-// float bits) or the table coordinate of T (kCellXq).
-template <int NBT>
+// One cell chord of length ds >= 0 (a zero-length chord, where the ray grazes
+// an edge or corner, adds nothing and is not counted as a step): density rho,
+// and aux = Lambda (kCellLam, as float bits) or the table coordinate of T
+// (kCellXq). With dtau = 0 (kappa_b = 0 or rho = 0) the Taylor form gives the
+// optically thin term j ds T exactly, so no separate case is needed.
+template <int NBT, int FMT>
 __device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t aux, float ds,
                                         const BandCtx &bc, const BandRegs<NBT> &br) {
   kahan_add(r.N, r.cN, rho * ds);
-  r.steps += 1;
+  r.steps += ds > 0.f ? 1u : 0u;
   int k = 0;
   float w = 0.f, lam1 = 1.f;
-  if (bc.fmt == kCellXq) {
+  if (FMT == kCellXq) {
     k = (int)(aux >> kXqFracBits);
     w = (float)(aux & ((1u << kXqFracBits) - 1u)) * (1.0f / (float)(1u << kXqFracBits));
-  } else if (bc.fmt == kCellLam) {
+  } else if (FMT == kCellLam) {
     lam1 = __uint_as_float(aux);
   }
   const float rho2ds = rho * rho * ds;
 #pragma unroll
   for (int b = 0; b < NBT; ++b) {
-    if (b < bc.nbh) {
+    if (NBT == 1 || b < bc.nbh) {
       float lam = lam1;
-      if (bc.fmt == kCellXq) {
+      if (FMT == kCellXq) {
         const float *t = bc.tab + b * bc.tstride + k;
         lam = fmaf(w, t[1] - t[0], t[0]);
       }
-      const float alpha = br.kap[b] * rho;
-      const float dtau = alpha * ds;
-      float term;
-      if (dtau > 0.f) {
-        kahan_add(r.tau[b], r.ctau[b], dtau);
-        const float Tn = __expf(-r.tau[b]);
-        if (dtau < 0.25f)
-          term = rho2ds * lam * r.T[b] * one_minus_exp_over_x(dtau);
-        else
-          term = rho * lam * br.ik[b] * (r.T[b] - Tn);
-        r.T[b] = Tn;
-      } else {
-        term = rho2ds * lam * r.T[b];
-      }
+      const float dtau = br.kap[b] * rho * ds;
+      kahan_add(r.tau[b], r.ctau[b], dtau);
+      const float Tn = __expf(-r.tau[b]);
+      const float term = dtau < 0.25f ? (rho2ds * lam) * (r.T[b] * one_minus_exp_over_x(dtau))
+                                      : (rho * lam * br.ik[b]) * (r.T[b] - Tn);
+      r.T[b] = Tn;
       kahan_add(r.I[b], r.cI[b], term);
     }
   }
 }
 
+// Cells of a block requested ahead of the march along its dominant axis.
+constexpr int kPrefetchAhead = 3;
+
 // Fields of cell idx: rho and the auxiliary word of the format.
-template <typename Idx>
-__device__ __forceinline__ void load_cell(const void *__restrict__ cells, int fmt, Idx idx,
-                                          float &rho, uint32_t &aux) {
-  if (fmt == kCellRho) {
+template <int FMT, typename Idx>
+__device__ __forceinline__ void load_cell(const void *__restrict__ cells, Idx idx, float &rho,
+                                          uint32_t &aux) {
+  if (FMT == kCellRho) {
     rho = __ldg((const float *)cells + idx);
     aux = 0u;
   } else {
@@ -127,62 +124,95 @@ __device__ __forceinline__ void load_cell(const void *__restrict__ cells, int fm
   }
 }
 
+// Ask L1 for the record of cell idx (a hint: nothing is loaded into registers).
+template <int FMT, typename Idx>
+__device__ __forceinline__ void prefetch_cell(const void *__restrict__ cells, Idx idx) {
+  const void *p = FMT == kCellRho ? (const void *)((const float *)cells + idx)
+                                  : (const void *)((const uint2 *)cells + idx);
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // DDA through a block of nx x ny x nz cells, entered in cell (lx, ly, lz).
 // Q: entry point relative to the low corner of the entry cell (in cells),
-// Dl: direction (cells per unit t), tend: block exit relative to the entry.
-// cells points at the block's cell (0, 0, 0); cell (x, y, z) is record
-// z*sz + y*sy + x. Boundary parameters are measured from the entry cell, so
-// their FP32 rounding grows with the distance marched inside the block, not
-// with the ray's distance from the origin. The fields of the next cell are
-// fetched before the current cell's transfer step, so the load latency
-// overlaps that arithmetic. Per-axis state is kept in scalars (registers).
-template <int NBT, typename Idx>
+// Dl: direction (cells per unit t), inv = 1 / Dl (0 where Dl = 0), tend:
+// block exit relative to the entry. cells points at the block's cell
+// (0, 0, 0); cell (x, y, z) is record z*sz + y*sy + x.
+//
+// After k steps along axis a the next face of that axis is crossed at
+// t = (k + [Dl > 0] - Q) / Dl = k |inv| + q, evaluated as one fused
+// multiply-add from the exact float count k, so the rounding of a boundary
+// parameter does not grow with the number of cells marched. Parameters are
+// measured from the entry cell, so their FP32 rounding scales with the
+// distance marched inside the block, not with the ray's distance from the
+// origin. The fields of the next cell are fetched before the current cell's
+// transfer step, so the load latency overlaps that arithmetic, and the cell
+// kPrefetchAhead steps further along the axis the ray crosses fastest is
+// requested from L1 at every step (clamped into the block), so most loads
+// find their line already on the way.
+template <int NBT, int FMT, typename Idx>
 __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], const float Dl[3],
-                                            float tend, int lx, int ly, int lz, int nx, int ny,
-                                            int nz, Idx sy, Idx sz, const void *__restrict__ cells,
-                                            const BandCtx &bc, const BandRegs<NBT> &br) {
+                                            const float inv[3], float tend, int lx, int ly, int lz,
+                                            int nx, int ny, int nz, Idx sy, Idx sz,
+                                            const void *__restrict__ cells, const BandCtx &bc,
+                                            const BandRegs<NBT> &br) {
   const float INF = FLT_MAX;
-  const int s0 = Dl[0] > 0.f ? 1 : -1, s1 = Dl[1] > 0.f ? 1 : -1, s2 = Dl[2] > 0.f ? 1 : -1;
-  const int p0 = Dl[0] > 0.f, p1 = Dl[1] > 0.f, p2 = Dl[2] > 0.f;
-  const float i0 = Dl[0] != 0.f ? 1.0f / Dl[0] : 0.f;
-  const float i1 = Dl[1] != 0.f ? 1.0f / Dl[1] : 0.f;
-  const float i2 = Dl[2] != 0.f ? 1.0f / Dl[2] : 0.f;
-  const Idx d0 = (Idx)s0, d1 = (Idx)s1 * sy, d2 = (Idx)s2 * sz;
-  int r0 = 0, r1 = 0, r2 = 0;  // cells stepped from the entry cell
-  float tm0 = Dl[0] != 0.f ? ((float)p0 - Q[0]) * i0 : INF;
-  float tm1 = Dl[1] != 0.f ? ((float)p1 - Q[1]) * i1 : INF;
-  float tm2 = Dl[2] != 0.f ? ((float)p2 - Q[2]) * i2 : INF;
+  const bool p0 = Dl[0] > 0.f, p1 = Dl[1] > 0.f, p2 = Dl[2] > 0.f;
+  const float a0 = fabsf(inv[0]), a1 = fabsf(inv[1]), a2 = fabsf(inv[2]);
+  const float q0 = Dl[0] != 0.f ? ((p0 ? 1.f : 0.f) - Q[0]) * inv[0] : INF;
+  const float q1 = Dl[1] != 0.f ? ((p1 ? 1.f : 0.f) - Q[1]) * inv[1] : INF;
+  const float q2 = Dl[2] != 0.f ? ((p2 ? 1.f : 0.f) - Q[2]) * inv[2] : INF;
+  // last step count that stays inside the block, per axis
+  const float km0 = (float)(p0 ? nx - 1 - lx : lx);
+  const float km1 = (float)(p1 ? ny - 1 - ly : ly);
+  const float km2 = (float)(p2 ? nz - 1 - lz : lz);
+  const Idx d0 = p0 ? (Idx)1 : (Idx)-1, d1 = p1 ? sy : -sy, d2 = p2 ? sz : -sz;
+  float k0 = 0.f, k1 = 0.f, k2 = 0.f;
+  float tm0 = q0, tm1 = q1, tm2 = q2;
   Idx idx = (Idx)lz * sz + (Idx)ly * sy + (Idx)lx;
+  const float e0 = fabsf(Dl[0]), e1 = fabsf(Dl[1]), e2 = fabsf(Dl[2]);
+  const Idx pstep = (e0 >= e1 && e0 >= e2) ? d0 : (e1 >= e2 ? d1 : d2);
+  const Idx plast = (Idx)nz * sz - 1;
   float rh;
   uint32_t xv;
-  load_cell(cells, bc.fmt, idx, rh, xv);
+  load_cell<FMT>(cells, idx, rh, xv);
+#pragma unroll
+  for (int n = 2; n <= kPrefetchAhead; ++n) {
+    const Idx pi = idx + (Idx)n * pstep;
+    prefetch_cell<FMT>(cells, pi < 0 ? (Idx)0 : (pi > plast ? plast : pi));
+  }
   float tl = 0.f;
   for (;;) {
     const float tn = fminf(fminf(tm0, tm1), fminf(tm2, tend));
-    const float ds = tn - tl;
+    const float ds = fmaxf(tn - tl, 0.f);
     bool more = tn < tend;
     float rh_n = 0.f;
     uint32_t xv_n = 0u;
     if (more) {
       if (tm0 <= tm1 && tm0 <= tm2) {
-        r0 += s0;
-        more = (unsigned)(lx + r0) < (unsigned)nx;
+        k0 += 1.f;
+        more = k0 <= km0;
         idx += d0;
-        tm0 = ((float)(r0 + p0) - Q[0]) * i0;
+        tm0 = fmaf(k0, a0, q0);
       } else if (tm1 <= tm2) {
-        r1 += s1;
-        more = (unsigned)(ly + r1) < (unsigned)ny;
+        k1 += 1.f;
+        more = k1 <= km1;
         idx += d1;
-        tm1 = ((float)(r1 + p1) - Q[1]) * i1;
+        tm1 = fmaf(k1, a1, q1);
       } else {
-        r2 += s2;
-        more = (unsigned)(lz + r2) < (unsigned)nz;
+        k2 += 1.f;
+        more = k2 <= km2;
         idx += d2;
-        tm2 = ((float)(r2 + p2) - Q[2]) * i2;
+        tm2 = fmaf(k2, a2, q2);
       }
-      if (more) load_cell(cells, bc.fmt, idx, rh_n, xv_n);
+      if (more) {
+        load_cell<FMT>(cells, idx, rh_n, xv_n);
+        if (kPrefetchAhead > 1) {
+          const Idx pi = idx + (Idx)kPrefetchAhead * pstep;
+          prefetch_cell<FMT>(cells, pi < 0 ? (Idx)0 : (pi > plast ? plast : pi));
+        }
+      }
     }
-    if (ds > 0.f) rt_cell<NBT>(r, rh, xv, ds, bc, br);
+    rt_cell<NBT, FMT>(r, rh, xv, ds, bc, br);
     if (!more) break;  // left the block (through its far face, or by rounding)
     rh = rh_n;
     xv = xv_n;
@@ -198,6 +228,9 @@ struct RayGeom {
   double C[3], U[3], V[3], h[3], invh[3], D[3], invD[3];
   double H, pix0;  // image half-extent, pixel size at level 0
   float Dhi[3], Dlo[3];  // D as a double-float pair
+  float invDhi[3];       // 1 / Dhi, correctly rounded (0 where D = 0); for a
+                         // brick at 2^s finest cells per cell, 1 / (Dhi 2^-s)
+                         // is exactly invDhi 2^s
 };
 
 // 2^-L exactly (0 <= L < 1023).
@@ -242,22 +275,24 @@ __device__ __forceinline__ bool ray_setup(const GridView &g, const RayGeom &rg, 
 
 __device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
 
-template <int NBT>
+template <int NBT, int FMT>
 __device__ void march_uniform(RTState<NBT> &r, const GridView &g, const double O[3],
-                              const double D[3], double t0, const BandCtx &bc,
+                              const RayGeom &rg, double t0, const BandCtx &bc,
                               const BandRegs<NBT> &br) {
-  float Q[3], Dl[3];
+  float Q[3], Dl[3], inv[3];
   int lc[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double F = O[a] + t0 * D[a];
+    const double F = O[a] + t0 * rg.D[a];
     lc[a] = clampi((int)floor(F), 0, g.nf[a] - 1);
     Q[a] = (float)(F - (double)lc[a]);
-    Dl[a] = (float)D[a];
+    Dl[a] = rg.Dhi[a];
+    inv[a] = rg.invDhi[a];
   }
   // the ray leaves through a face of the grid: no end parameter needed
-  march_block<NBT, int64_t>(r, Q, Dl, FLT_MAX, lc[0], lc[1], lc[2], g.nf[0], g.nf[1], g.nf[2],
-                            (int64_t)g.nf[0], (int64_t)g.nf[0] * g.nf[1], g.cells, bc, br);
+  march_block<NBT, FMT, int64_t>(r, Q, Dl, inv, FLT_MAX, lc[0], lc[1], lc[2], g.nf[0], g.nf[1],
+                                 g.nf[2], (int64_t)g.nf[0], (int64_t)g.nf[0] * g.nf[1], g.cells,
+                                 bc, br);
 }
 
 // Double-float helpers (error-free transformations: Knuth's TwoSum and the
@@ -297,9 +332,38 @@ __device__ __forceinline__ float f2_offset(F2 O, F2 t, F2 D, float anchor) {
   return a + ((se + O.lo) + pe);
 }
 
-// Per-launch constants (direction, its inverse and its double-float split)
-// are read from the kernel-parameter bank, not held per thread.
-template <int NBT>
+// Dense brick-map entry of finest cell c (see GridView::bmap).
+__device__ __forceinline__ int map_entry(const GridView &g, int c0, int c1, int c2) {
+  const int sm = g.log2B + g.Lm - g.mapL;
+  return __ldg(g.bmap + ((int64_t)(c2 >> sm) * g.nm[1] + (c1 >> sm)) * g.nm[0] + (c0 >> sm));
+}
+
+// Leaf brick holding finest cell c from its map entry: id, and its level in
+// `lev`. Below the map level the brick octree is descended.
+__device__ __forceinline__ int brick_of(const GridView &g, int e, const int c[3], int &lev) {
+  if (e >= 0) {
+    lev = e >> kMapLevelShift;
+    return e & kMapIdMask;
+  }
+  const int s0 = g.log2B + g.Lm;
+  lev = g.mapL;
+  while (e < 0) {
+    ++lev;
+    const int sh = s0 - lev;
+    const int oc = ((c[0] >> sh) & 1) | (((c[1] >> sh) & 1) << 1) | (((c[2] >> sh) & 1) << 2);
+    e = __ldg(g.oct + (int64_t)(-e - 1) * 8 + oc);
+  }
+  return e;
+}
+
+// Brick by brick: find the leaf brick holding finest cell c, compute the
+// entry point in it and the exit face (FP64 at levels >= fp64_level, else
+// double-float), march its cells, step to the finest cell across the exit
+// face. The map entry of the next brick is fetched before the current brick
+// is marched, so its latency overlaps the march. Per-launch constants
+// (direction, its inverse and its double-float split) are read from the
+// kernel-parameter bank, not held per thread.
+template <int NBT, int FMT>
 __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
                           const RayGeom &rg, double t0, int fp64_level, const BandCtx &bc,
                           const BandRegs<NBT> &br) {
@@ -314,33 +378,27 @@ __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
   }
   F2 t = f2_from(t0);
   const int max_iter = 4 * (g.nf[0] + g.nf[1] + g.nf[2]);
-  const int s0 = lb + Lm;
+  int e = map_entry(g, c[0], c[1], c[2]);
   for (int it = 0; it < max_iter; ++it) {
-    // leaf brick holding finest cell c
-    int code = __ldg(g.base + ((int64_t)(c[2] >> s0) * g.nb0[1] + (c[1] >> s0)) * g.nb0[0] + (c[0] >> s0));
-    int lev = 0;
-    while (code < 0) {
-      ++lev;
-      const int sh = s0 - lev;
-      const int oc = ((c[0] >> sh) & 1) | (((c[1] >> sh) & 1) << 1) | (((c[2] >> sh) & 1) << 2);
-      code = __ldg(g.oct + (int64_t)(-code - 1) * 8 + oc);
-    }
-    const int4 bi = __ldg(g.binfo + code);
-    r.maxlev = max(r.maxlev, bi.w);
-    const int bo[3] = {bi.x, bi.y, bi.z};
-    const int shift = Lm - bi.w;
+    int lev;
+    const int code = brick_of(g, e, c, lev);
+    r.maxlev = max(r.maxlev, lev);
+    const int shift = Lm - lev;
+    const int sb = lb + shift;
     const int S = B << shift;
-    const float scale = 1.0f / (float)(1 << shift);
-    int lc[3], anchor[3];
+    const float scale = __int_as_float((127 - shift) << 23);  // 2^-shift
+    const float up = __int_as_float((127 + shift) << 23);     // 2^shift
+    int lc[3], anchor[3], bo[3];
     float Q[3], Dl[3], inv[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
+      bo[a] = (c[a] >> sb) << sb;
       lc[a] = (c[a] - bo[a]) >> shift;
       anchor[a] = bo[a] + (lc[a] << shift);
       Dl[a] = rg.Dhi[a] * scale;
-      inv[a] = Dl[a] != 0.f ? 1.0f / Dl[a] : 0.f;
+      inv[a] = rg.invDhi[a] * up;
     }
-    const bool deep = bi.w >= fp64_level;
+    const bool deep = lev >= fp64_level;
     // entry point relative to the entry cell, and the exit face: smallest
     // parameter over the axes, measured from the entry
     float tend = FLT_MAX;
@@ -352,8 +410,8 @@ __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         Q[a] = (float)(fma(td, D[a], O[a] - (double)anchor[a]) * (double)scale);
-        if (D[a] != 0.0) {
-          const double face = (double)(D[a] > 0.0 ? bo[a] + S : bo[a]);
+        if (Dl[a] != 0.f) {
+          const double face = (double)(Dl[a] > 0.f ? bo[a] + S : bo[a]);
           const double ta = (face - O[a]) * invD[a];
           if (ta < tmin) {
             tmin = ta;
@@ -381,34 +439,40 @@ __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
       }
       if (tend < 0.f) tend = 0.f;
     }
-    const int64_t boff = (int64_t)code << (3 * lb);
-    const void *cb = g.cell_fmt == kCellRho ? (const void *)((const float *)g.cells + boff)
-                                            : (const void *)((const uint2 *)g.cells + boff);
-    march_block<NBT, int>(r, Q, Dl, tend, lc[0], lc[1], lc[2], B, B, B, B, B * B, cb, bc, br);
-    if (ax < 0) break;
-    // advance to the exit point
-    if (deep) t = f2_from(te);
-    else t = f2_add_f(t, tend);
     // finest cell just across the exit face; the other coordinates, from the
     // exit point in this brick's frame, stay in this brick's range
-    bool out = false;
+    bool out = ax < 0;
+    int cn[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       if (a == ax) {
-        c[a] = D[a] > 0.0 ? bo[a] + S : bo[a] - 1;
-        out = c[a] < 0 || c[a] >= g.nf[a];
+        cn[a] = Dl[a] > 0.f ? bo[a] + S : bo[a] - 1;
+        out = out || cn[a] < 0 || cn[a] >= g.nf[a];
       } else {
-        const float e = fmaf(tend, Dl[a], Q[a]);  // local cells from the entry cell
-        const int f = anchor[a] + (int)floorf(e * (float)(1 << shift));
-        c[a] = clampi(f, bo[a], bo[a] + S - 1);
+        const float x = fmaf(tend, Dl[a], Q[a]);  // local cells from the entry cell
+        const int f = anchor[a] + (int)floorf(x * up);
+        cn[a] = clampi(f, bo[a], bo[a] + S - 1);
       }
     }
+    const int en = out ? 0 : map_entry(g, cn[0], cn[1], cn[2]);
+    const int64_t boff = (int64_t)code << (3 * lb);
+    const void *cb = FMT == kCellRho ? (const void *)((const float *)g.cells + boff)
+                                     : (const void *)((const uint2 *)g.cells + boff);
+    march_block<NBT, FMT, int>(r, Q, Dl, inv, tend, lc[0], lc[1], lc[2], B, B, B, B, B * B, cb,
+                               bc, br);
     if (out) break;
+    // advance to the exit point
+    if (deep) t = f2_from(te);
+    else t = f2_add_f(t, tend);
+    c[0] = cn[0];
+    c[1] = cn[1];
+    c[2] = cn[2];
+    e = en;
   }
 }
 
 // One ray (pixel (L, i, j)) through the grid, bands [b0, b0 + NBT) of bc/br.
-template <int NBT, bool AMR>
+template <int NBT, bool AMR, int FMT>
 __device__ __forceinline__ void trace_ray(RTState<NBT> &st, const GridView &g, const RayGeom &rg,
                                           int L, int i, int j, int fp64_level, const BandCtx &bc,
                                           const BandRegs<NBT> &br) {
@@ -416,9 +480,9 @@ __device__ __forceinline__ void trace_ray(RTState<NBT> &st, const GridView &g, c
   double O[3], t0;
   if (ray_setup(g, rg, L, i, j, O, t0)) {
     if (AMR)
-      march_amr<NBT>(st, g, O, rg, t0, fp64_level, bc, br);
+      march_amr<NBT, FMT>(st, g, O, rg, t0, fp64_level, bc, br);
     else
-      march_uniform<NBT>(st, g, O, rg.D, t0, bc, br);
+      march_uniform<NBT, FMT>(st, g, O, rg, t0, bc, br);
   }
 }
 
@@ -434,7 +498,15 @@ static inline RayGeom make_geom(const GridView &g, const Camera &cam, int n0) {
     rg.D[a] = cam.d[a] / g.h[a];
     rg.invD[a] = cam.d[a] != 0.0 ? 1.0 / rg.D[a] : 0.0;
     rg.Dhi[a] = (float)rg.D[a];
+    // a direction component too small for FP32 (the ray moves less than
+    // 1e-30 cells per unit length along that axis) is taken as zero
+    if (!(fabsf(rg.Dhi[a]) >= 1e-30f)) {
+      rg.D[a] = 0.0;
+      rg.invD[a] = 0.0;
+      rg.Dhi[a] = 0.f;
+    }
     rg.Dlo[a] = (float)(rg.D[a] - (double)rg.Dhi[a]);
+    rg.invDhi[a] = rg.Dhi[a] != 0.f ? 1.0f / rg.Dhi[a] : 0.f;
   }
   rg.H = cam.H;
   rg.pix0 = (2.0 * cam.H) / (double)n0;
