@@ -359,7 +359,7 @@ struct EmitOutV {
     if (o.N) o.N[r] = t.N[k];
     if (o.p) o.p[r] = t.p[k];
     const double pix = geoms[v].pix0;
-    const double area = pix * pix / (double)(1ull << (2 * t.lvl[k]));
+    const double area = pix * pix * __longlong_as_double((long long)(1023 - 2 * t.lvl[k]) << 52);
     for (int b = 0; b < o.n_bands; ++b) {
       const float I = t.I[(int64_t)b * t.cap + k];
       if (o.I) o.I[(int64_t)b * o.stride + r] = I;

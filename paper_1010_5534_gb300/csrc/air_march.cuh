@@ -73,7 +73,9 @@ __device__ __forceinline__ void rt_init(RTState<NBT> &r) {
 // an edge or corner, adds nothing and is not counted as a step): density rho,
 // and aux = Lambda (kCellLam, as float bits) or the table coordinate of T
 // (kCellXq). With dtau = 0 (kappa_b = 0 or rho = 0) the Taylor form gives the
-// optically thin term j ds T exactly, so no separate case is needed.
+// optically thin term j ds T exactly, so no separate case is needed. Both
+// forms of the cell term are evaluated and one is selected, which keeps the
+// march loop free of divergent branches.
 template <int NBT, int FMT>
 __device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t aux, float ds,
                                         const BandCtx &bc, const BandRegs<NBT> &br) {
@@ -99,8 +101,9 @@ __device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t aux
       const float dtau = br.kap[b] * rho * ds;
       kahan_add(r.tau[b], r.ctau[b], dtau);
       const float Tn = __expf(-r.tau[b]);
-      const float term = dtau < 0.25f ? (rho2ds * lam) * (r.T[b] * one_minus_exp_over_x(dtau))
-                                      : (rho * lam * br.ik[b]) * (r.T[b] - Tn);
+      const float t_small = (rho2ds * lam) * (r.T[b] * one_minus_exp_over_x(dtau));
+      const float t_large = (rho * lam * br.ik[b]) * (r.T[b] - Tn);
+      const float term = dtau < 0.25f ? t_small : t_large;
       r.T[b] = Tn;
       kahan_add(r.I[b], r.cI[b], term);
     }
@@ -148,7 +151,9 @@ __device__ __forceinline__ void prefetch_cell(const void *__restrict__ cells, Id
 // transfer step, so the load latency overlaps that arithmetic, and the cell
 // kPrefetchAhead steps further along the axis the ray crosses fastest is
 // requested from L1 at every step (clamped into the block), so most loads
-// find their line already on the way.
+// find their line already on the way. The loop body is straight-line code
+// (the axis to step, the next index and the transfer form are selected, not
+// branched on); its one branch is the exit from the block.
 template <int NBT, int FMT, typename Idx>
 __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], const float Dl[3],
                                             const float inv[3], float tend, int lx, int ly, int lz,
@@ -184,39 +189,32 @@ __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], c
   for (;;) {
     const float tn = fminf(fminf(tm0, tm1), fminf(tm2, tend));
     const float ds = fmaxf(tn - tl, 0.f);
-    bool more = tn < tend;
-    float rh_n = 0.f;
-    uint32_t xv_n = 0u;
-    if (more) {
-      if (tm0 <= tm1 && tm0 <= tm2) {
-        k0 += 1.f;
-        more = k0 <= km0;
-        idx += d0;
-        tm0 = fmaf(k0, a0, q0);
-      } else if (tm1 <= tm2) {
-        k1 += 1.f;
-        more = k1 <= km1;
-        idx += d1;
-        tm1 = fmaf(k1, a1, q1);
-      } else {
-        k2 += 1.f;
-        more = k2 <= km2;
-        idx += d2;
-        tm2 = fmaf(k2, a2, q2);
-      }
-      if (more) {
-        load_cell<FMT>(cells, idx, rh_n, xv_n);
-        if (kPrefetchAhead > 1) {
-          const Idx pi = idx + (Idx)kPrefetchAhead * pstep;
-          prefetch_cell<FMT>(cells, pi < 0 ? (Idx)0 : (pi > plast ? plast : pi));
-        }
-      }
+    tl = tn;
+    // step the axis whose face comes first (selects, no branches); an axis
+    // that is not stepped keeps its count and so its boundary parameter
+    const bool x0 = tm0 <= tm1 && tm0 <= tm2;
+    const bool x1 = !x0 && tm1 <= tm2;
+    const bool x2 = !x0 && !x1;
+    k0 += x0 ? 1.f : 0.f;
+    k1 += x1 ? 1.f : 0.f;
+    k2 += x2 ? 1.f : 0.f;
+    tm0 = fmaf(k0, a0, q0);
+    tm1 = fmaf(k1, a1, q1);
+    tm2 = fmaf(k2, a2, q2);
+    const bool more = tn < tend && k0 <= km0 && k1 <= km1 && k2 <= km2;
+    const Idx nidx = idx + (x0 ? d0 : (x1 ? d1 : d2));
+    idx = more ? nidx : idx;  // past the block: reload the current cell (no use)
+    float rh_n;
+    uint32_t xv_n;
+    load_cell<FMT>(cells, idx, rh_n, xv_n);
+    if (kPrefetchAhead > 1) {
+      const Idx pi = idx + (Idx)kPrefetchAhead * pstep;
+      prefetch_cell<FMT>(cells, pi < 0 ? (Idx)0 : (pi > plast ? plast : pi));
     }
     rt_cell<NBT, FMT>(r, rh, xv, ds, bc, br);
     if (!more) break;  // left the block (through its far face, or by rounding)
     rh = rh_n;
     xv = xv_n;
-    tl = tn;
   }
 }
 

@@ -177,21 +177,36 @@ __global__ void k_init_base(TreeView t) {
 
 // ---- band flux and step count --------------------------------------------
 // Per block: sum over selected pixels of I_b x area(level) in FP64 and of the
-// step counts; a second kernel adds the block partials in block order.
+// step counts (integers); a second kernel adds the block partials of each
+// band in a fixed order (strided per thread, then a tree), so the result does
+// not depend on scheduling. area(level) = area0 4^-L is an exact power-of-two
+// scaling, applied as a product.
+__device__ __forceinline__ double pow4_neg(int L) {
+  return __longlong_as_double((long long)(1023 - 2 * L) << 52);
+}
+
 __global__ void __launch_bounds__(256) k_flux_partial(FluxArgs a) {
   __shared__ double sh[256];
+  __shared__ unsigned long long shs[256];
   const int64_t start = (int64_t)blockIdx.x * a.per_block;
   const int64_t end = min(a.n, start + a.per_block);
   double *outp = a.partial + (int64_t)blockIdx.x * (a.n_bands + 1);
-  for (int b = -1; b < a.n_bands; ++b) {
+  unsigned long long st = 0;
+  for (int64_t k = start + threadIdx.x; k < end; k += blockDim.x) st += a.steps[k];
+  shs[threadIdx.x] = st;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (threadIdx.x < off) shs[threadIdx.x] += shs[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) outp[0] = (double)shs[0];
+  for (int b = 0; b < a.n_bands; ++b) {
     double s = 0.0;
     for (int64_t k = start + threadIdx.x; k < end; k += blockDim.x) {
       const bool leaf = a.child ? a.child[k] < 0 : true;
-      if (b < 0) {
-        s += (double)a.steps[k];
-      } else if (leaf) {
+      if (leaf) {
         const int L = a.lvl ? a.lvl[k] : 0;
-        s += (double)a.I[(int64_t)b * a.stride + k] * a.area0 / (double)(1ull << (2 * L));
+        s += (double)a.I[(int64_t)b * a.stride + k] * a.area0 * pow4_neg(L);
       }
     }
     sh[threadIdx.x] = s;
@@ -205,14 +220,23 @@ __global__ void __launch_bounds__(256) k_flux_partial(FluxArgs a) {
   }
 }
 
-__global__ void k_flux_final(const double *partial, int64_t nblocks, int n_bands, double *flux,
-                             double *steps) {
-  const int b = (int)threadIdx.x - 1;
-  if (b >= n_bands) return;
+// One block per output: block 0 the step count, block b + 1 band b.
+__global__ void __launch_bounds__(256) k_flux_final(const double *partial, int64_t nblocks,
+                                                    int n_bands, double *flux, double *steps) {
+  __shared__ double sh[256];
+  const int b = (int)blockIdx.x - 1;
   double s = 0.0;
-  for (int64_t x = 0; x < nblocks; ++x) s += partial[x * (n_bands + 1) + b + 1];
-  if (b < 0) *steps = s;
-  else flux[b] = s;
+  for (int64_t x = threadIdx.x; x < nblocks; x += blockDim.x) s += partial[x * (n_bands + 1) + b + 1];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (b < 0) *steps = sh[0];
+    else flux[b] = sh[0];
+  }
 }
 
 // ---- host launchers ----------------------------------------------------------
@@ -296,7 +320,7 @@ cudaError_t launch_flux(FluxArgs a, double *flux, double *steps, cudaStream_t st
     return cudaMemsetAsync(steps, 0, sizeof(double), st);
   }
   k_flux_partial<<<(unsigned)nb, 256, 0, st>>>(a);
-  k_flux_final<<<1, ((a.n_bands + 1 + 31) / 32) * 32, 0, st>>>(a.partial, nb, a.n_bands, flux, steps);
+  k_flux_final<<<(unsigned)(a.n_bands + 1), 256, 0, st>>>(a.partial, nb, a.n_bands, flux, steps);
   return cudaGetLastError();
 }
 

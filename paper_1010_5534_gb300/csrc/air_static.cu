@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(256) k_flux_static_partial(
     for (int64_t k = start + threadIdx.x; k < end; k += blockDim.x) {
       if (is_leaf && !is_leaf[k]) continue;
       const int L = level ? level[k] : 0;
-      s += (double)I[(int64_t)b * stride + k] * area0 / (double)(1ull << (2 * L));
+      s += (double)I[(int64_t)b * stride + k] * area0 * __longlong_as_double((long long)(1023 - 2 * L) << 52);
     }
     sh[threadIdx.x] = s;
     __syncthreads();

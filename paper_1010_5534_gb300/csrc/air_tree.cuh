@@ -19,25 +19,53 @@ __device__ __forceinline__ int descend(const TreeView &t, int base0, int L, int 
   return k;
 }
 
-// Eq. 2 on the 3x3 stencil s[3*(dj+1) + (di+1)], FP64 with every operation
-// rounded separately (no fused multiply-add), in a fixed order.
-__device__ __forceinline__ double xi_eq2(const double s[9], int xi_norm) {
+// Numerator and denominator of Eq. 2 (squared) on the 3x3 stencil
+// s[3*(dj+1) + (di+1)], FP64 with every operation rounded separately (no
+// fused multiply-add), in a fixed order.
+__device__ __forceinline__ void xi_terms(const double s[9], int xi_norm, double &num, double &den) {
   const double c = s[4], xm = s[3], xp = s[5], ym = s[1], yp = s[7];
   const double mm = s[0], pm = s[2], mp = s[6], pp = s[8];
   const double c2 = __dmul_rn(2.0, c);
   const double d2u = __dadd_rn(__dsub_rn(xp, c2), xm);
   const double d2v = __dadd_rn(__dsub_rn(yp, c2), ym);
   const double duv = __dmul_rn(__dadd_rn(__dsub_rn(__dsub_rn(pp, pm), mp), mm), 0.25);
-  const double num = __dadd_rn(__dadd_rn(__dmul_rn(d2u, d2u), __dmul_rn(d2v, d2v)),
-                               __dmul_rn(2.0, __dmul_rn(duv, duv)));
+  num = __dadd_rn(__dadd_rn(__dmul_rn(d2u, d2u), __dmul_rn(d2v, d2v)),
+                  __dmul_rn(2.0, __dmul_rn(duv, duv)));
   const double au = __dadd_rn(fabs(__dsub_rn(xp, c)), fabs(__dsub_rn(c, xm)));
   const double av = __dadd_rn(fabs(__dsub_rn(yp, c)), fabs(__dsub_rn(c, ym)));
-  double den = __dadd_rn(__dmul_rn(au, au), __dmul_rn(av, av));
+  den = __dadd_rn(__dmul_rn(au, au), __dmul_rn(av, av));
   if (xi_norm == 1) den = __dmul_rn(2.0, den);
+}
+
+// xi of Eq. 2: 0 where the numerator vanishes, 1 where only the denominator
+// does, sqrt(num / den) (correctly rounded quotient and root) clamped to 1.
+__device__ __forceinline__ double xi_eq2(const double s[9], int xi_norm) {
+  double num, den;
+  xi_terms(s, xi_norm, num, den);
   if (num == 0.0) return 0.0;
   if (den == 0.0) return 1.0;
   const double x = __dsqrt_rn(__ddiv_rn(num, den));
   return x > 1.0 ? 1.0 : x;
+}
+
+// xi_eq2(s) >= xi_crit, decided without the quotient and root where num is
+// clearly above or below den xi_crit^2: the margin 2^-40 exceeds the rounding
+// of the products and of the quotient and root by a factor of about 2^12,
+// so every decision equals the comparison of the rounded xi. Inside the
+// margin the rounded xi is computed and compared.
+__device__ __forceinline__ bool xi_at_least(const double s[9], int xi_norm, double xi_crit) {
+  if (!(xi_crit > 0.0)) return true;
+  if (xi_crit > 1.0) return false;
+  double num, den;
+  xi_terms(s, xi_norm, num, den);
+  if (num == 0.0) return false;
+  if (den == 0.0) return true;
+  const double c2 = __dmul_rn(xi_crit, xi_crit);
+  const double m = 9.094947017729282e-13;  // 2^-40
+  if (num >= __dmul_rn(den, __dmul_rn(c2, 1.0 + m))) return true;
+  if (num <= __dmul_rn(den, __dmul_rn(c2, 1.0 - m))) return false;
+  const double x = __dsqrt_rn(__ddiv_rn(num, den));
+  return (x > 1.0 ? 1.0 : x) >= xi_crit;
 }
 
 // Step iii for node k: 1 if it is a leaf below max_level with xi >= xi_crit.
@@ -60,12 +88,12 @@ __device__ __forceinline__ uint32_t xi_flag(const TreeView &t, int base0, int64_
   if (refine_on == 0 || refine_on == 2) {
 #pragma unroll
     for (int m = 0; m < 9; ++m) s[m] = (double)t.p[q[m]];
-    f |= xi_eq2(s, xi_norm) >= xi_crit;
+    f |= xi_at_least(s, xi_norm, xi_crit);
   }
   if (refine_on == 1 || refine_on == 2) {
 #pragma unroll
     for (int m = 0; m < 9; ++m) s[m] = (double)t.N[q[m]];
-    f |= xi_eq2(s, xi_norm) >= xi_crit;
+    f |= xi_at_least(s, xi_norm, xi_crit);
   }
   return f;
 }
