@@ -190,11 +190,7 @@ __global__ void __launch_bounds__(kBatchBlock) k_air_batch(BatchArgs a) {
         bc.tstride = tstride;
         bc.nbh = min(NBT, nb - b0);
         BandRegs<NBT> br;
-#pragma unroll
-        for (int q = 0; q < NBT; ++q) {
-          br.kap[q] = q < bc.nbh ? __ldg(g.kappa + b0 + q) : 0.f;
-          br.ik[q] = q < bc.nbh ? __ldg(g.invkappa + b0 + q) : 0.f;
-        }
+        band_regs<NBT>(br, g.kappa, g.invkappa, b0, bc.nbh);
         const RayGeom rg = a.geoms[v];
         RTState<NBT> st;
         trace_ray<NBT, AMR, FMT>(st, g, rg, t.lvl[k], t.pi[k], t.pj[k], a.fp64_level, bc, br);

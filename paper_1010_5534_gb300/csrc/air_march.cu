@@ -25,11 +25,7 @@ __global__ void __launch_bounds__(kMarchBlock, MinBlocks<NBT>::value)
   if (FMT == kCellXq)
     for (int x = threadIdx.x; x < nbh * tstride; x += blockDim.x) smem[x] = g.table[b0 * tstride + x];
   BandRegs<NBT> br;
-#pragma unroll
-  for (int b = 0; b < NBT; ++b) {
-    br.kap[b] = b < nbh ? __ldg(g.kappa + b0 + b) : 0.f;
-    br.ik[b] = b < nbh ? __ldg(g.invkappa + b0 + b) : 0.f;
-  }
+  band_regs<NBT>(br, g.kappa, g.invkappa, b0, nbh);
   __syncthreads();
 
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -60,7 +56,7 @@ __global__ void __launch_bounds__(kMarchBlock, MinBlocks<NBT>::value)
   if (chunk == 0) {
     out.N[k] = st.N;
     out.steps[k] = st.steps;
-    if (out.tau0) out.tau0[k] = st.tau[0];
+    if (out.tau0) out.tau0[k] = br.kap[0] * st.N;
     if (out.maxlev) out.maxlev[k] = (uint8_t)st.maxlev;
   }
 #pragma unroll

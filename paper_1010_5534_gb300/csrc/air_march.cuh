@@ -20,12 +20,14 @@
 // entry point is expressed relative to the entry cell, so FP32 rounding inside
 // a brick scales with the distance marched in it.
 //
-// Accumulation in FP32: N, tau_b and I_b are Kahan-compensated sums;
-// T = exp(-tau) is recomputed from the compensated tau at every cell (CUDA's
-// __expf intrinsic: at most 2 + floor(1.17 |tau|) ulp, and no error carried
-// from one cell to the next); the cell
-// term is j ds T (1 - e^-dtau)/dtau from a Taylor polynomial for dtau < 1/4,
-// and (j/alpha)(T_prev - T_next) above.
+// Accumulation in FP32: N and I_b are Kahan-compensated sums. The absorption
+// coefficient is alpha_b = kappa_b rho with kappa_b fixed per band, so the
+// optical depth is tau_b = kappa_b N exactly, taken from the compensated N;
+// T_b = e^-tau_b = 2^(-kappa_b log2(e) N) is recomputed at every cell with the
+// hardware base-2 exponential (ex2.approx: relative error about 2^-22, plus
+// the rounding of its argument, |tau| 2^-24 relative), so no error is carried
+// from one cell to the next. The cell term is j ds T (1 - e^-dtau)/dtau from
+// a Taylor polynomial for dtau < 1/4, and (j/alpha)(T_prev - T_next) above.
 #pragma once
 #include <cfloat>
 
@@ -36,7 +38,7 @@ namespace air {
 template <int NBT>
 struct RTState {
   float N, cN;
-  float tau[NBT], ctau[NBT], T[NBT], I[NBT], cI[NBT];
+  float T[NBT], I[NBT], cI[NBT];
   uint32_t steps;
   int maxlev;  // deepest brick level crossed
 };
@@ -51,7 +53,27 @@ template <int NBT>
 struct BandRegs {
   float kap[NBT];  // kappa_b
   float ik[NBT];   // 1 / kappa_b (0 where kappa_b = 0)
+  float nk[NBT];   // -kappa_b log2(e): T_b = 2^(nk_b N)
 };
+
+// Per-band registers of bands [b0, b0 + nbh) (zero beyond).
+template <int NBT>
+__device__ __forceinline__ void band_regs(BandRegs<NBT> &br, const float *kappa,
+                                          const float *invkappa, int b0, int nbh) {
+#pragma unroll
+  for (int b = 0; b < NBT; ++b) {
+    br.kap[b] = b < nbh ? __ldg(kappa + b0 + b) : 0.f;
+    br.ik[b] = b < nbh ? __ldg(invkappa + b0 + b) : 0.f;
+    br.nk[b] = (float)(-(double)br.kap[b] * 1.4426950408889634);
+  }
+}
+
+// 2^x by the hardware approximation (PTX ex2.approx.ftz.f32).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 template <int NBT>
 __device__ __forceinline__ void rt_init(RTState<NBT> &r) {
@@ -61,8 +83,6 @@ __device__ __forceinline__ void rt_init(RTState<NBT> &r) {
   r.maxlev = 0;
 #pragma unroll
   for (int b = 0; b < NBT; ++b) {
-    r.tau[b] = 0.f;
-    r.ctau[b] = 0.f;
     r.T[b] = 1.f;
     r.I[b] = 0.f;
     r.cI[b] = 0.f;
@@ -79,7 +99,8 @@ __device__ __forceinline__ void rt_init(RTState<NBT> &r) {
 template <int NBT, int FMT>
 __device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t aux, float ds,
                                         const BandCtx &bc, const BandRegs<NBT> &br) {
-  kahan_add(r.N, r.cN, rho * ds);
+  const float rds = rho * ds;
+  kahan_add(r.N, r.cN, rds);
   r.steps += ds > 0.f ? 1u : 0u;
   int k = 0;
   float w = 0.f, lam1 = 1.f;
@@ -89,7 +110,7 @@ __device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t aux
   } else if (FMT == kCellLam) {
     lam1 = __uint_as_float(aux);
   }
-  const float rho2ds = rho * rho * ds;
+  const float rho2ds = rho * rds;
 #pragma unroll
   for (int b = 0; b < NBT; ++b) {
     if (NBT == 1 || b < bc.nbh) {
@@ -98,9 +119,8 @@ __device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t aux
         const float *t = bc.tab + b * bc.tstride + k;
         lam = fmaf(w, t[1] - t[0], t[0]);
       }
-      const float dtau = br.kap[b] * rho * ds;
-      kahan_add(r.tau[b], r.ctau[b], dtau);
-      const float Tn = __expf(-r.tau[b]);
+      const float dtau = br.kap[b] * rds;
+      const float Tn = ex2_approx(br.nk[b] * r.N);
       const float t_small = (rho2ds * lam) * (r.T[b] * one_minus_exp_over_x(dtau));
       const float t_large = (rho * lam * br.ik[b]) * (r.T[b] - Tn);
       const float term = dtau < 0.25f ? t_small : t_large;
@@ -153,13 +173,63 @@ __device__ __forceinline__ void prefetch_cell(const void *__restrict__ cells, Id
 // requested from L1 at every step (clamped into the block), so most loads
 // find their line already on the way. The loop body is straight-line code
 // (the axis to step, the next index and the transfer form are selected, not
-// branched on); its one branch is the exit from the block.
+// branched on); its one branch is the exit from the block. A ray parallel to
+// a grid axis takes a one-axis form of the same loop (one boundary parameter,
+// one counter, one bound); the per-launch direction makes this choice the
+// same for every thread.
 template <int NBT, int FMT, typename Idx>
 __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], const float Dl[3],
                                             const float inv[3], float tend, int lx, int ly, int lz,
                                             int nx, int ny, int nz, Idx sy, Idx sz,
                                             const void *__restrict__ cells, const BandCtx &bc,
                                             const BandRegs<NBT> &br) {
+  if (Dl[0] == 0.f ? (Dl[1] == 0.f) != (Dl[2] == 0.f) : (Dl[1] == 0.f && Dl[2] == 0.f)) {
+    // the ray is parallel to one grid axis (a face-on view): a one-axis DDA
+    const int ax = Dl[0] != 0.f ? 0 : (Dl[1] != 0.f ? 1 : 2);
+    const float D1 = ax == 0 ? Dl[0] : (ax == 1 ? Dl[1] : Dl[2]);
+    const float i1 = ax == 0 ? inv[0] : (ax == 1 ? inv[1] : inv[2]);
+    const float Q1 = ax == 0 ? Q[0] : (ax == 1 ? Q[1] : Q[2]);
+    const int l1 = ax == 0 ? lx : (ax == 1 ? ly : lz);
+    const int n1 = ax == 0 ? nx : (ax == 1 ? ny : nz);
+    const Idx s1 = ax == 0 ? (Idx)1 : (ax == 1 ? sy : sz);
+    const bool pos = D1 > 0.f;
+    const float a1 = fabsf(i1);
+    const float q1 = ((pos ? 1.f : 0.f) - Q1) * i1;
+    const float km = (float)(pos ? n1 - 1 - l1 : l1);
+    const Idx d1 = pos ? s1 : -s1;
+    const Idx plast = (Idx)nz * sz - 1;
+    Idx idx = (Idx)lz * sz + (Idx)ly * sy + (Idx)lx;
+    float rh;
+    uint32_t xv;
+    load_cell<FMT>(cells, idx, rh, xv);
+#pragma unroll
+    for (int n = 2; n <= kPrefetchAhead; ++n) {
+      const Idx pi = idx + (Idx)n * d1;
+      prefetch_cell<FMT>(cells, pi < 0 ? (Idx)0 : (pi > plast ? plast : pi));
+    }
+    float k1 = 0.f, tm = q1, tl = 0.f;
+    for (;;) {
+      const float tn = fminf(tm, tend);
+      const float ds = fmaxf(tn - tl, 0.f);
+      tl = tn;
+      k1 += 1.f;
+      tm = fmaf(k1, a1, q1);
+      const bool more = tn < tend && k1 <= km;
+      idx = more ? idx + d1 : idx;
+      float rh_n;
+      uint32_t xv_n;
+      load_cell<FMT>(cells, idx, rh_n, xv_n);
+      if (kPrefetchAhead > 1) {
+        const Idx pi = idx + (Idx)kPrefetchAhead * d1;
+        prefetch_cell<FMT>(cells, pi < 0 ? (Idx)0 : (pi > plast ? plast : pi));
+      }
+      rt_cell<NBT, FMT>(r, rh, xv, ds, bc, br);
+      if (!more) break;
+      rh = rh_n;
+      xv = xv_n;
+    }
+    return;
+  }
   const float INF = FLT_MAX;
   const bool p0 = Dl[0] > 0.f, p1 = Dl[1] > 0.f, p2 = Dl[2] > 0.f;
   const float a0 = fabsf(inv[0]), a1 = fabsf(inv[1]), a2 = fabsf(inv[2]);
