@@ -45,7 +45,8 @@ class Scene(C.Structure):
                 ("brick_origin", C.c_void_p), ("rho", C.c_void_p), ("temp", C.c_void_p),
                 ("n_bands", C.c_int32), ("emis_mode", C.c_int32),
                 ("lambda_table", C.c_void_p), ("n_tbins", C.c_int32),
-                ("logT_lo", C.c_double), ("logT_hi", C.c_double), ("kappa", C.c_void_p)]
+                ("logT_lo", C.c_double), ("logT_hi", C.c_double), ("kappa", C.c_void_p),
+                ("field_f32", C.c_int32)]
 
 
 class ViewS(C.Structure):
@@ -113,7 +114,8 @@ def _view(v) -> ViewS:
 
 
 class Oracle:
-    """Holds a prepared scene (FP64 copies of the fields) for repeated calls."""
+    """Holds a prepared scene for repeated calls. FP32 fields are read in place
+    (each value widens exactly to FP64 on use), others as FP64 copies."""
 
     def __init__(self, scene):
         self.scene = scene
@@ -123,10 +125,13 @@ class Oracle:
         s.n[:] = [int(x) for x in scene.n]
         s.lo[:] = [float(x) for x in scene.lo]
         s.hi[:] = [float(x) for x in scene.hi]
-        self.rho = np.ascontiguousarray(scene.rho, dtype=np.float64)
+        f32 = scene.rho.dtype == np.float32 and (scene.temp is None or scene.temp.dtype == np.float32)
+        fdt = np.float32 if f32 else np.float64
+        s.field_f32 = 1 if f32 else 0
+        self.rho = np.ascontiguousarray(scene.rho, dtype=fdt)
         s.rho = _p(self.rho)
         if scene.temp is not None:
-            self.temp = np.ascontiguousarray(scene.temp, dtype=np.float64)
+            self.temp = np.ascontiguousarray(scene.temp, dtype=fdt)
             s.temp = _p(self.temp)
         if scene.kind == "amr":
             self.blev = np.ascontiguousarray(scene.brick_level, dtype=np.int32)

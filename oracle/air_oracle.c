@@ -54,6 +54,11 @@ void orc_release(orc_ctx *c) {
   free(c);
 }
 
+/* Cell value id of a field stored as double or float (a float widens exactly). */
+static double field_at(const orc_scene *s, const void *f, int64_t id) {
+  return s->field_f32 ? (double)((const float *)f)[id] : ((const double *)f)[id];
+}
+
 orc_ctx *orc_prepare(const orc_scene *s, int32_t *err) {
   *err = ORC_ERR_ARG;
   if (!s || !s->rho || s->n_bands < 1 || s->n_bands > ORC_MAX_BANDS || !s->kappa) return NULL;
@@ -177,14 +182,14 @@ typedef struct {
  * of the transfer equation with constant source function j/alpha. */
 static void add_chord(const orc_ctx *c, ray_acc *r, int64_t id, double ds) {
   const orc_scene *s = &c->s;
-  double rho = s->rho[id];
+  double rho = field_at(s, s->rho, id);
   r->col += rho * ds;
   r->steps += 1;
   for (int b = 0; b < s->n_bands; ++b) {
     double alpha = s->kappa[b] * rho;
     double dtau = alpha * ds;
     double j = rho * rho;
-    if (s->emis_mode == 1) j *= orc_lambda(c, b, s->temp[id]);
+    if (s->emis_mode == 1) j *= orc_lambda(c, b, field_at(s, s->temp, id));
     double att = exp(-r->tau[b]);
     double term = (alpha > 0.0) ? (j / alpha) * (-expm1(-dtau)) * att : j * ds * att;
     r->inten[b] += term;

@@ -38,13 +38,14 @@ typedef struct {
   int32_t brick, max_level, n_bricks;
   const int32_t *brick_level;
   const int32_t *brick_origin;
-  const double *rho;
-  const double *temp;          /* NULL allowed when emis_mode == 0 */
+  const void *rho;             /* double, or float when field_f32 (read exactly as double) */
+  const void *temp;            /* NULL allowed when emis_mode == 0 */
   int32_t n_bands, emis_mode;  /* emis_mode 0: j = rho^2 ; 1: j = rho^2 Lambda_b(T) */
   const double *lambda_table;  /* [n_bands][n_tbins] */
   int32_t n_tbins;
   double logT_lo, logT_hi;
   const double *kappa;         /* [n_bands], opacity per unit density */
+  int32_t field_f32;           /* 1: rho and temp are float arrays */
 } orc_scene;
 
 typedef struct {

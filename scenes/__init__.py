@@ -18,6 +18,7 @@ Every random number is drawn from numpy's PCG64 with an explicit seed.
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -305,6 +306,158 @@ def cone_shock_amr(seed: int = 0, n_base: int = 128, brick: int = 16, levels: in
         sc.rho_smooth = smooth
         sc.clump_sigma = clump_sigma
     return sc
+
+
+def clumps_cones_amr(seed: int = 0, n_base: int = 512, brick: int = 32, levels: int = 5,
+                     n_clumps: int = 200, r_range=(0.005, 0.02), contrast=(10.0, 1000.0),
+                     clump_factor: float = 1.0, cone_levels: int = 0, n_bands: int = 32,
+                     e_lo: float = 0.5, e_hi: float = 10.0, kappa0: float = 0.3,
+                     half_angle_deg: float = 30.0, thickness: float = 0.04,
+                     clump_sigma: float = 0.3, n_tbins: int = 64) -> Scene:
+    """Large block-AMR scene over [-1,1]^3: two colliding-wind shock cones and
+    n_clumps dense clumps.
+
+    Winds: rho_w = |x - s1|^-2 + |x - s2|^-2 (floored at 0.05), stars
+    s1 = (-0.8, 0, 0), s2 = (0.8, 0.1, 0). Cones: apex (-0.5, 0, 0) axis +x and
+    apex (0.5, 0.1, 0) axis -x, half-angle 30 deg; shell of thickness 0.04 at
+    4x density and T = 10^7.5 K, interior 0.25x; elsewhere T = 10^4 K.
+    Clumps: centres uniform in [-0.8, 0.8]^3, radii log-uniform in r_range,
+    density contrast log-uniform in `contrast`, T = 10^5 K inside. Every cell
+    carries lognormal clumping exp(0.3 z - 0.045), z ~ N(0,1) per cell.
+
+    Refinement (factor 2 per level, `levels` levels): a brick is refined while
+    it intersects a clump of radius r and its edge exceeds clump_factor * r;
+    bricks within a half-diagonal + thickness/2 of a cone surface are refined
+    below level cone_levels (0: the cones stay at the base resolution, where
+    the shell is 10 base cells thick at n_base 512). Fields are FP32, sampled
+    at the cell centres of each leaf brick at its own level; the per-cell
+    normals come from one PCG64 stream per chunk of 2^21 cells, spawned from
+    SeedSequence([seed, 1]), so the fields do not depend on how the chunks are
+    scheduled over threads."""
+    assert n_base % brick == 0
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lo, hi = -1.0, 1.0
+    nf = n_base << levels
+    hf = (hi - lo) / nf
+    half_angle = math.radians(half_angle_deg)
+    cr = np.exp(rng.uniform(math.log(r_range[0]), math.log(r_range[1]), n_clumps))
+    cc = rng.uniform(-0.8, 0.8, size=(n_clumps, 3))
+    cf = np.exp(rng.uniform(math.log(contrast[0]), math.log(contrast[1]), n_clumps))
+    stars = ((-0.8, 0.0, 0.0), (0.8, 0.1, 0.0))
+    cones = (((-0.5, 0.0, 0.0), 1.0), ((0.5, 0.1, 0.0), -1.0))
+
+    def cone_d(px, py, pz, apex, sgn):
+        a = sgn * (px - apex[0])
+        r = np.sqrt((py - apex[1]) ** 2 + (pz - apex[2]) ** 2)
+        ct, st = math.cos(half_angle), math.sin(half_angle)
+        on = a * ct + r * st >= 0.0
+        d = np.where(on, r * ct - a * st, np.sqrt(a * a + r * r))
+        return d, on
+
+    nb0 = n_base // brick
+    g = np.arange(nb0)
+    bz, by, bx = np.meshgrid(g, g, g, indexing="ij")
+    cur = np.stack([bx.ravel(), by.ravel(), bz.ravel()], axis=1).astype(np.int64) * (brick << levels)
+    leaf_levels, leaf_origins = [], []
+    for lev in range(levels + 1):
+        S = brick << (levels - lev)
+        size = S * hf
+        ref = np.zeros(len(cur), dtype=bool)
+        if lev < levels and len(cur):
+            blo = lo + cur * hf
+            bhi = blo + size
+            for k in range(n_clumps):
+                if size > clump_factor * cr[k]:
+                    q = np.clip(cc[k], blo, bhi)
+                    ref |= ((q - cc[k]) ** 2).sum(axis=1) <= cr[k] ** 2
+            if lev < cone_levels:
+                ctr = blo + size / 2
+                for apex, sgn in cones:
+                    d, _ = cone_d(ctr[:, 0], ctr[:, 1], ctr[:, 2], apex, sgn)
+                    ref |= np.abs(d) <= math.sqrt(3.0) * size / 2 + thickness / 2
+        keep = cur[~ref]
+        leaf_levels.append(np.full(len(keep), lev, dtype=np.int32))
+        leaf_origins.append(keep)
+        rr = cur[ref]
+        h = S // 2
+        kids = [rr + np.array([dx * h, dy * h, dz * h], dtype=np.int64)
+                for dz in (0, 1) for dy in (0, 1) for dx in (0, 1)]
+        cur = np.concatenate(kids, axis=0) if len(rr) else np.zeros((0, 3), np.int64)
+        if len(cur):
+            cur = cur[np.lexsort((cur[:, 0], cur[:, 1], cur[:, 2]))]
+    levels_arr = np.concatenate(leaf_levels)
+    origins = np.concatenate(leaf_origins, axis=0)
+    nb = len(levels_arr)
+
+    rho = np.empty((nb, brick, brick, brick), dtype=np.float32)
+    temp = np.empty((nb, brick, brick, brick), dtype=np.float32)
+    off = (np.arange(brick) + 0.5).astype(np.float64)
+    ct, st = math.cos(half_angle), math.sin(half_angle)
+    f32 = np.float32
+    chunk = max(1, (1 << 21) // brick ** 3)
+    starts = list(range(0, nb, chunk))
+    streams = np.random.SeedSequence([seed, 1]).spawn(len(starts))
+
+    def fill(ci):
+        c0 = starts[ci]
+        sel = np.arange(c0, min(nb, c0 + chunk))
+        m = len(sel)
+        step = (1 << (levels - levels_arr[sel])).astype(np.float64)
+        o = origins[sel].astype(np.float64)
+        # cell-centre coordinates per axis, [m, B] (float32 after the FP64 sum)
+        cx = (lo + (o[:, 0:1] + off[None, :] * step[:, None]) * hf).astype(f32)
+        cy = (lo + (o[:, 1:2] + off[None, :] * step[:, None]) * hf).astype(f32)
+        cz = (lo + (o[:, 2:3] + off[None, :] * step[:, None]) * hf).astype(f32)
+        X = cx[:, None, None, :]
+        Y = cy[:, None, :, None]
+        Z = cz[:, :, None, None]
+        rho_w = np.zeros((m, brick, brick, brick), dtype=f32)
+        for s_ in stars:
+            ryz2 = (Y - f32(s_[1])) ** 2 + (Z - f32(s_[2])) ** 2            # [m, B, B, 1]
+            rw = np.sqrt((X - f32(s_[0])) ** 2 + ryz2)
+            rho_w += np.maximum(rw, f32(0.05)) ** -2
+        fac = np.ones_like(rho_w)
+        tv = np.full(rho_w.shape, f32(1e4))
+        for apex, sgn in cones:
+            a = f32(sgn) * (X - f32(apex[0]))                                # [m, 1, 1, B]
+            r = np.sqrt((Y - f32(apex[1])) ** 2 + (Z - f32(apex[2])) ** 2)  # [m, B, B, 1]
+            on = a * f32(ct) + r * f32(st) >= 0
+            d = np.where(on, r * f32(ct) - a * f32(st), np.sqrt(a * a + r * r))
+            shell = (np.abs(d) <= f32(thickness / 2)) & on
+            inside = (d < f32(-thickness / 2)) & on
+            fac = np.where(shell, fac * f32(4.0), np.where(inside, fac * f32(0.25), fac))
+            tv = np.where(shell, f32(10.0 ** 7.5), tv)
+        # clumps: only those whose sphere meets a brick of this chunk
+        h = 0.5 * step[:, None] * hf
+        blo = np.stack([cx[:, 0], cy[:, 0], cz[:, 0]], axis=1) - h
+        bhi = blo + brick * step[:, None] * hf
+        for k in range(n_clumps):
+            q = np.clip(cc[k], blo, bhi)
+            hit = np.nonzero(((q - cc[k]) ** 2).sum(axis=1) <= cr[k] ** 2)[0]
+            if len(hit) == 0:
+                continue
+            ck = cc[k].astype(f32)
+            r2 = (X[hit] - ck[0]) ** 2 + (Y[hit] - ck[1]) ** 2 + (Z[hit] - ck[2]) ** 2
+            inn = r2 <= f32(cr[k] ** 2)
+            fac[hit] = np.where(inn, fac[hit] * f32(cf[k]), fac[hit])
+            tv[hit] = np.where(inn, f32(1e5), tv[hit])
+        zr = np.random.Generator(np.random.PCG64(streams[ci]))
+        z = zr.standard_normal(m * brick ** 3, dtype=np.float32).reshape(rho_w.shape)
+        clump = np.exp(f32(clump_sigma) * z - f32(0.5 * clump_sigma ** 2))
+        rho[sel] = rho_w * fac * clump
+        temp[sel] = tv
+
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(fill, range(len(starts))))
+
+    edges = band_edges(n_bands, e_lo, e_hi)
+    return Scene(kind="amr", lo=(lo,) * 3, hi=(hi,) * 3, n=(n_base,) * 3, rho=rho, temp=temp,
+                 brick=brick, max_level=levels, brick_level=levels_arr,
+                 brick_origin=origins.astype(np.int32), emis_mode=1,
+                 lambda_table=cooling_table(edges, n_tbins), logT_lo=4.0, logT_hi=9.0,
+                 kappa=band_kappa(edges, kappa0),
+                 name=f"clumps_cones_{n_base}^3_b{brick}_L{levels}_{n_clumps}cl_{n_bands}band_s{seed}")
 
 
 def reseed(scene: Scene, seed: int) -> Scene:
