@@ -376,6 +376,115 @@ def run_learned(args):
         "total_s": time.perf_counter() - t0}), flush=True)
 
 
+LARGE = dict(workload="clumps-and-cones block-AMR grid: 512^3 base cells in 32^3 bricks, 5 "
+                       "refinement levels (16384^3 effective) around 200 dense clumps (r 0.005-"
+                       "0.02, contrast 10-1000) with two shock cones at the base resolution, "
+                       "FP32 rho/T (1.06 G cells), 32 bands (0.5-10 keV) with absorption; 16 "
+                       "random views; AIR base 1024^2, max level 3 (8192^2 equivalent), "
+                       "xi_crit 0.5", seed=0, views=16, base_res=1024, max_level=3, xi_crit=0.5,
+             fixed_res=8192)
+FP32_OPS_PER_BAND_STEP = 23  # per band and cell: dtau, exponent argument, Taylor (7), both
+                             # cell-term forms (7), select, Kahan sum (4), table lookup (2)
+
+
+def run_large(args):
+    """The large configuration: 16 views x 32 bands of the clumps-and-cones
+    grid as one batched persistent render, the same views one by one, the
+    learned proposal (network trained on plain trees of 48 other views of the
+    same grid) view by view, and fixed 8192^2 images (two views timed)."""
+    import torch
+    import paper_1010_5534_gb300 as air
+    from oracle import mlp as omlp
+    air.build()
+    W = LARGE
+    n0, Lm, xc = W["base_res"], W["max_level"], W["xi_crit"]
+    t0 = time.perf_counter()
+    sc = scenes.clumps_cones_amr(W["seed"])
+    gen_s = time.perf_counter() - t0
+    t = time.perf_counter()
+    g = air.Grid(sc)
+    torch.cuda.synchronize()
+    load_s = time.perf_counter() - t
+    vs = scenes.random_views(21, W["views"])
+    st = torch.cuda.current_stream()
+    out = {"workload": W["workload"], "cells": int(sc.n_cells), "bricks": int(len(sc.brick_level)),
+           "bricks_per_level": np.bincount(sc.brick_level).tolist(), "scene_gen_s": gen_s,
+           "grid_upload_s": load_s}
+    # batched plain AIR
+    batch = {}
+    for bpt in (8, 16):
+        g.render_batch(vs, n0, Lm, xc, bands_per_thread=bpt, fields=("band_flux",))
+        g.profile(True)
+        ms, b = _timed(lambda: g.render_batch(vs, n0, Lm, xc, bands_per_thread=bpt,
+                                              fields=("band_flux",)), st)
+        prof = g.profile_read()
+        g.profile(False)
+        steps = sum(r["n_steps"] for r in b)
+        batch[f"bands_per_thread_{bpt}"] = dict(ms=ms, rays=sum(r["n_rays"] for r in b), steps=steps,
+                                                band_steps_per_s=sc.n_bands * steps / ms * 1e3,
+                                                kernel_ms=prof["batch"][0])
+    best = min(batch.values(), key=lambda r: r["ms"])
+    out["batch"] = batch
+    # the same views one by one
+    g.render_adaptive(vs[0], n0, Lm, xc, fields=("band_flux",))
+    ms_seq, seq = _timed(lambda: [g.render_adaptive(v, n0, Lm, xc, fields=("band_flux",))
+                                  for v in vs], st)
+    out["sequential_ms"] = ms_seq
+    out["batch_speedup_vs_sequential"] = ms_seq / best["ms"]
+    out["batch_equal_to_sequential"] = all(a["n_rays"] == b_["n_rays"] and a["n_steps"] == b_["n_steps"]
+                                           for a, b_ in zip(seq, b))
+    # learned proposal
+    t = time.perf_counter()
+    xs, ys = [], []
+    for v in scenes.random_views(22, 48):
+        x, y = g.learn_samples(v, n0, Lm, xc)
+        xs.append(x)
+        ys.append(y)
+    X, Y = torch.cat(xs), torch.cat(ys)
+    del xs, ys
+    torch.cuda.synchronize()
+    data_s = time.perf_counter() - t
+    net = air.MLP(omlp.init(0, scale=1.0))
+    t = time.perf_counter()
+    net.train(X, Y, batch=8192, epochs=4, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t
+    g.render_learned(vs[0], n0, Lm, xc, net, quantile=0.8)
+    ms_l, rl = _timed(lambda: [g.render_learned(v, n0, Lm, xc, net, quantile=0.8) for v in vs], st)
+    same = all(bool((p["intensity"] == q[0]["intensity"]).all()) and bool((p["level"] == q[0]["level"]).all())
+               for p, q in zip([g.render_adaptive(v, n0, Lm, xc) for v in vs[:2]], rl[:2]))
+    out["learned"] = dict(samples=int(X.shape[0]), label_counts=torch.bincount(Y.long(), minlength=5)
+                          .cpu().tolist(), data_s=data_s, train_s=train_s, ms=ms_l,
+                          waves=float(np.mean([q[1]["waves"] for q in rl])),
+                          plain_waves=float(np.mean([1 + r["n_sweeps"] for r in seq])),
+                          wasted_rays=int(sum(q[1]["wasted_rays"] for q in rl)),
+                          speedup_vs_sequential=ms_seq / ms_l, first_two_identical=same)
+    del X, Y
+    # fixed 8192^2 (two views timed)
+    g.render_fixed(vs[0], 1024, fields=("band_flux",))
+    fx = []
+    for v in vs[:2]:
+        ms_f, f = _timed(lambda: g.render_fixed(v, W["fixed_res"], fields=("band_flux",)), st)
+        fx.append(dict(ms=ms_f, steps=f["n_steps"]))
+    fixed_view_ms = float(np.mean([x["ms"] for x in fx]))
+    out["fixed_per_view_ms"] = fixed_view_ms
+    out["fixed_16_views_ms_extrapolated"] = fixed_view_ms * W["views"]
+    out["batch_speedup_vs_fixed"] = fixed_view_ms * W["views"] / best["ms"]
+    for k in range(2):
+        fs = g.render_fixed(vs[k], W["fixed_res"], fields=("band_flux",))
+        fa = fs["band_flux"].double().sum().item()
+        out.setdefault("flux_rel_err_vs_fixed", []).append(
+            abs(seq[k]["band_flux"].double().sum().item() - fa) / abs(fa))
+    # ALU roofline of the batched kernel: FP32 operations per band-step
+    peak_ops = 152 * 128 * 2.07e9
+    ach = best["band_steps_per_s"] * FP32_OPS_PER_BAND_STEP
+    out["roofline"] = {"bound": "alu", "achieved": ach / 1e12, "peak": peak_ops / 1e12,
+                       "unit": "T FP32 op/s", "frac": ach / peak_ops, "traffic": None,
+                       "kernel": "k_air_batch", "ops_per_band_step": FP32_OPS_PER_BAND_STEP}
+    out["total_s"] = time.perf_counter() - t0
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -383,7 +492,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="air", choices=["air", "batch", "learned", "ring"],
+    ap.add_argument("--workload", default="air", choices=["air", "batch", "learned", "ring", "large"],
                     help="air: the benchmark line (one adaptive image of the cone grid); "
                          "batch: 64 views x 16 bands in one persistent launch vs one by one; "
                          "learned: train the depth network on 2000 plain trees, evaluate")
@@ -401,6 +510,8 @@ def main():
         return run_learned(args)
     if args.workload == "ring":
         return run_ring(args)
+    if args.workload == "large":
+        return run_large(args)
     assert args.warmup >= 3 or args.profile_case, "at least 3 warm-up steps"
 
     import torch

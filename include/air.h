@@ -279,6 +279,33 @@ AIR_API air_status air_profile_enable(air_grid *g, int32_t on);
  * phase p < AIR_N_PHASES (either pointer may be NULL). */
 AIR_API air_status air_profile_read(air_grid *g, double *ms, int64_t *launches);
 
+/* Finest-level raster of the most recent single-view adaptive image on this
+ * handle (air_render_adaptive or air_render_learned; a batched render or
+ * air_free ends it). Section 2 step vi allows the output image's edges to be
+ * sharpened by interpolating between adjacent pixels of differing resolution
+ * (a super-resolution step; the paper fixes no method). With base n0 and
+ * max level Lm of that render, out holds (n0 2^Lm)^2 floats, row-major
+ * [y][x], y along v:
+ *   AIR_RASTER_NEAREST : each finest pixel takes the value of its leaf;
+ *   AIR_RASTER_BILINEAR: with L the level of that leaf, the pixel centre is
+ *     placed on the level-L pixel grid, u = (x + 1/2) 2^(L - Lm) - 1/2 (v
+ *     likewise), and the value is the bilinear interpolation between the
+ *     four level-L pixels floor(u) + {0,1} x floor(v) + {0,1}, indices
+ *     clamped to the image; a level-L pixel's value is that of the deepest
+ *     traced node at level <= L covering it (the refinement scan's neighbour
+ *     rule). Finest-level leaves keep their values exactly.
+ * quantity: AIR_RASTER_INTENSITY (band `band`), AIR_RASTER_SUM (band-summed
+ * intensity), AIR_RASTER_COLDENS (column density). out: device or host
+ * memory (detected), caller-owned, n_out floats. Computed in FP32 on the
+ * handle's stream; the call returns after out is written.
+ * Errors: AIR_ERR_ARG (NULL out, unknown quantity or mode, band out of range,
+ * no image to rasterise), AIR_ERR_CAPACITY (n_out < (n0 2^Lm)^2; nothing is
+ * written), AIR_ERR_CUDA. */
+enum { AIR_RASTER_NEAREST = 0, AIR_RASTER_BILINEAR = 1 };
+enum { AIR_RASTER_INTENSITY = 0, AIR_RASTER_SUM = 1, AIR_RASTER_COLDENS = 2 };
+AIR_API air_status air_render_raster(air_grid *g, int32_t quantity, int32_t band, int32_t mode,
+                                     float *out, int64_t n_out);
+
 /* Band flux of an image already in device memory, computed without allocating
  * any memory. The paper has no counterpart: this is a service for callers that
  * cannot call cudaMalloc when they need the flux -- a real-time or serving loop

@@ -23,20 +23,23 @@ _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_HERE, "libair_gb300.so")
 SOURCES = ["air_api.cu", "air_grid.cu", "air_march.cu", "air_refine.cu", "air_static.cu",
-           "air_batch.cu", "air_mlp.cu", "air_learned.cu", "air_tune.cu"]
+           "air_batch.cu", "air_mlp.cu", "air_learned.cu", "air_tune.cu", "air_raster.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 
 AIR_OK, AIR_ERR_ARG, AIR_ERR_OOM, AIR_ERR_CUDA, AIR_ERR_CAPACITY, AIR_ERR_TIMEOUT, \
     AIR_ERR_NUMERIC = range(7)
 AIR_HOST, AIR_DEVICE = 0, 1
+RASTER_MODES = {"nearest": 0, "bilinear": 1}
+RASTER_QUANTITIES = {"I": 0, "p": 1, "N": 2}
 
 EXPORTED = ["air_load_grid", "air_set_stream", "air_render_fixed", "air_render_adaptive",
             "air_render_batch", "air_mlp_create", "air_mlp_set_stream", "air_mlp_params",
             "air_mlp_forward", "air_mlp_loss_grad", "air_mlp_train", "air_mlp_free",
             "air_learn_samples", "air_render_learned", "air_autotune", "air_set_tuning",
             "air_get_tuning",
-            "air_profile_enable", "air_profile_read", "air_band_flux_static", "air_free",
+            "air_profile_enable", "air_profile_read", "air_band_flux_static", "air_render_raster",
+            "air_free",
             "air_last_error", "air_version"]
 PHASES = ("march", "scan", "balance", "refine", "output", "batch", "learn")
 
@@ -199,6 +202,9 @@ def lib():
             L.air_band_flux_static.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
                                                C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
                                                C.c_void_p]
+            L.air_render_raster.restype = C.c_int
+            L.air_render_raster.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                                            C.c_int64]
             L.air_free.restype = None
             L.air_free.argtypes = [C.c_void_p]
             L.air_last_error.restype = C.c_char_p
@@ -377,6 +383,7 @@ class Grid:
         if st == AIR_ERR_CAPACITY and all(im.n_out > 0 for im in ims):
             caps = [max(int(im.n_out), 1) for im in ims]
             st, ims, outs = _batch_call(self, views, p, o, caps, mem, fields)
+        self._raster_src = None
         _check(st)
         self._batch_hint = {k: int(im.n_out) for k, im in enumerate(ims)}
         return [self._result(im, out) for im, out in zip(ims, outs)]
@@ -417,6 +424,7 @@ class Grid:
                                           C.byref(o), C.byref(im), C.byref(stats))
         _check(st)
         self._cap_hint = max(self._cap_hint, int(im.n_out))
+        self._raster_src = (int(base_res), int(max_level))
         sd = {f: getattr(stats, f) for f, _ in LearnedStats._fields_}
         return self._result(im, out), sd
 
@@ -436,7 +444,24 @@ class Grid:
             st = lib().air_render_adaptive(self._h, C.byref(_view(view)), C.byref(p), C.byref(im))
         _check(st)
         self._cap_hint = max(self._cap_hint, int(im.n_out))
+        self._raster_src = (int(base_res), int(max_level))
         return self._result(im, out)
+
+    def raster(self, quantity="p", band=0, mode="bilinear", mem="device"):
+        """air_render_raster: finest-level raster [(n0 2^Lm), (n0 2^Lm)] (index
+        [y, x]) of the most recent single-view adaptive image, float32."""
+        import torch
+        src = getattr(self, "_raster_src", None)
+        if src is None:
+            raise AirError(AIR_ERR_ARG, "no single-view adaptive image to rasterise")
+        nf = src[0] << src[1]
+        out = torch.empty((nf, nf), dtype=torch.float32, device="cuda" if mem == "device" else "cpu",
+                          pin_memory=(mem != "device"))
+        _check(lib().air_set_stream(self._h, _stream()))
+        _check(lib().air_render_raster(self._h, RASTER_QUANTITIES[quantity], int(band),
+                                       RASTER_MODES[mode], C.c_void_p(out.data_ptr()),
+                                       C.c_int64(nf * nf)))
+        return out
 
 
 def _batch_call(grid, views, p, opts, caps, mem, fields):

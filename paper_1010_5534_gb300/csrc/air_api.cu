@@ -11,6 +11,7 @@
 namespace air {
 
 static thread_local char g_err[512] = "";
+void clear_error() { g_err[0] = 0; }
 
 air_status set_error(air_status s, const char *fmt, ...) {
   va_list ap;
@@ -291,6 +292,7 @@ air_status render_fixed(air_grid *g, const air_view *view, int32_t res, int32_t 
 }
 
 air_status render_adaptive(air_grid *g, const air_view *view, const air_params *pr, air_image *im) {
+  g->raster.ok = false;  // the workspace tree is about to change
   air_status s = check_image(im);
   if (s) return s;
   Camera cam;
@@ -409,6 +411,9 @@ air_status output_tree(air_grid *g, const Camera &cam, const air_params *pr, air
     return set_error(AIR_ERR_CAPACITY, "capacity %lld < %lld pixels", (long long)im->capacity, (long long)n_out);
   }
   g->last.valid = false;
+  g->raster.ok = true;
+  g->raster.n0 = n0;
+  g->raster.Lm = pr->max_level;
   CU_TRY(ensure((void **)&w.partial, &w.partial_b, sizeof(double) * (nb + 1) * flux_blocks(n)));
   FluxArgs fa{};
   fa.n = n; fa.child = t.child; fa.lvl = t.lvl; fa.I = t.I; fa.stride = t.cap; fa.steps = t.steps;

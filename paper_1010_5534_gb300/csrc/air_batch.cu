@@ -453,6 +453,7 @@ static int default_bands_per_thread(int nb) {
 
 air_status render_batch(air_grid *g, const air_view *views, int32_t V, const air_params *pr,
                         const air_batch_opts *opts, air_image *outs) {
+  g->raster.ok = false;  // the workspace tree is about to change
   if (!views || !outs || !pr) return set_error(AIR_ERR_ARG, "views, params and outs must not be NULL");
   if (V < 1 || V > kBatchMaxViews) return set_error(AIR_ERR_ARG, "n_views must be in [1, %d]", kBatchMaxViews);
   const int n0 = pr->base_res, Lm = pr->max_level;

@@ -171,6 +171,8 @@ void dfree(T *&p) {
 void free_grid_impl(air_grid *g) {
   dfree(g->d_cells); dfree(g->d_base); dfree(g->d_oct); dfree(g->d_bmap);
   dfree(g->d_table); dfree(g->d_kappa); dfree(g->d_invkappa);
+  dfree(g->raster.scratch);
+  g->raster.ok = false;
   free_batch(g);
   free_learn(g);
   Workspace &w = g->ws;

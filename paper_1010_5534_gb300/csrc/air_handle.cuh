@@ -8,6 +8,7 @@
 namespace air {
 
 air_status set_error(air_status s, const char *fmt, ...);
+void clear_error();  // empties the calling thread's error text
 air_status cuda_fail(cudaError_t e, const char *what);
 
 // Grows a device buffer to at least `bytes` (contents are not kept).
@@ -131,6 +132,14 @@ struct LearnWork {
          pp_b = 0, psteps_b = 0, missing_b = 0, counters_b = 0;
 };
 
+// The single-view tree that air_render_raster reads (set by output_tree).
+struct RasterSrc {
+  bool ok = false;
+  int n0 = 0, Lm = 0;
+  float *scratch = nullptr;  // device staging for host outputs
+  size_t scratch_b = 0;
+};
+
 struct LastRender {
   bool valid = false;
   air_view view;
@@ -152,6 +161,7 @@ struct air_grid {
   int64_t n_cells = 0;
   air::Workspace ws;
   air::LastRender last;
+  air::RasterSrc raster;
   air::Profiler prof;
   air::BatchWork batch;
   air::LearnWork learn;

@@ -335,6 +335,7 @@ air_status learn_samples(air_grid *g, const air_view *view, const air_params *pr
 
 air_status render_learned(air_grid *g, const air_view *view, const air_params *pr, air_mlp *mlp,
                           const air_learned_opts *opts, air_image *im, air_learned_stats *stats) {
+  g->raster.ok = false;  // the workspace tree is about to change
   air_status s = check_image(im);
   if (s) return s;
   Camera cam;
