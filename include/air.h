@@ -279,6 +279,29 @@ AIR_API air_status air_profile_enable(air_grid *g, int32_t on);
  * phase p < AIR_N_PHASES (either pointer may be NULL). */
 AIR_API air_status air_profile_read(air_grid *g, double *ms, int64_t *launches);
 
+/* Adaptive image whose per-node spectra go to host memory sweep by sweep
+ * instead of staying on the device. Section 2 notes that an integrated
+ * spectrum needs every pixel's spectrum kept until the calculation ends, and
+ * that writing them out during the calculation bounds the memory this takes.
+ * As air_render_adaptive, with params->include_interior = 1 required (the
+ * spectra are indexed by node, and out lists every traced node in creation
+ * order) and out->intensity NULL (not written). spectra: caller-owned
+ * page-locked host memory (cudaHostAlloc or cudaHostRegister), spectra_cap
+ * nodes x n_bands floats; node k's band b is spectra[b * spectra_cap + k].
+ * On the device each sweep's spectra go to one of two staging buffers, and a
+ * second stream copies them to `spectra` while the next sweep's scan and
+ * refinement run; the quadtree keeps only the band-summed intensity and the
+ * column density, so device memory no longer grows with n_bands x nodes.
+ * band_flux is computed by a kernel that reads `spectra` from host memory.
+ * The call returns after `spectra` and out are complete.
+ * Errors: as air_render_adaptive; AIR_ERR_ARG if spectra is not page-locked
+ * or include_interior != 1 or out->intensity is set; AIR_ERR_CAPACITY if
+ * spectra_cap is smaller than the number of traced nodes (out->n_rays set;
+ * the spectra are then incomplete) or out->capacity is too small. */
+AIR_API air_status air_render_adaptive_spectra(air_grid *g, const air_view *view,
+                                               const air_params *params, air_image *out,
+                                               float *spectra, int64_t spectra_cap);
+
 /* Finest-level raster of the most recent single-view adaptive image on this
  * handle (air_render_adaptive or air_render_learned; a batched render or
  * air_free ends it). Section 2 step vi allows the output image's edges to be

@@ -39,6 +39,7 @@ EXPORTED = ["air_load_grid", "air_set_stream", "air_render_fixed", "air_render_a
             "air_learn_samples", "air_render_learned", "air_autotune", "air_set_tuning",
             "air_get_tuning",
             "air_profile_enable", "air_profile_read", "air_band_flux_static", "air_render_raster",
+            "air_render_adaptive_spectra",
             "air_free",
             "air_last_error", "air_version"]
 PHASES = ("march", "scan", "balance", "refine", "output", "batch", "learn")
@@ -202,6 +203,9 @@ def lib():
             L.air_band_flux_static.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
                                                C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
                                                C.c_void_p]
+            L.air_render_adaptive_spectra.restype = C.c_int
+            L.air_render_adaptive_spectra.argtypes = [C.c_void_p, C.POINTER(View), C.POINTER(Params),
+                                                      C.POINTER(Image), C.c_void_p, C.c_int64]
             L.air_render_raster.restype = C.c_int
             L.air_render_raster.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
                                             C.c_int64]
@@ -446,6 +450,33 @@ class Grid:
         self._cap_hint = max(self._cap_hint, int(im.n_out))
         self._raster_src = (int(base_res), int(max_level))
         return self._result(im, out)
+
+    def render_adaptive_spectra(self, view, base_res, max_level, xi_crit, xi_norm=0, refine_on=0,
+                                fp64_level=-1, mem="device", fields=("level", "i", "j", "is_leaf",
+                                                                     "coldens", "p", "band_flux"),
+                                spectra_cap=None):
+        """air_render_adaptive_spectra: every traced node (creation order) and
+        its spectrum in a page-locked host tensor [n_bands, spectra_cap]
+        (float32, node k in column k). Returns (result, spectra)."""
+        import torch
+        fields = tuple(f for f in fields if f != "intensity")
+        _check(lib().air_set_stream(self._h, _stream()))
+        p = Params(int(base_res), int(max_level), float(xi_crit), int(xi_norm), int(refine_on),
+                   int(fp64_level), 1)
+        cap = spectra_cap or max(self._cap_hint, 4 * base_res * base_res)
+        for _ in range(2):
+            spec = torch.empty((self.n_bands, cap), dtype=torch.float32, pin_memory=True)
+            im, out = self._alloc(cap, mem, fields)
+            st = lib().air_render_adaptive_spectra(self._h, C.byref(_view(view)), C.byref(p),
+                                                   C.byref(im), C.c_void_p(spec.data_ptr()),
+                                                   C.c_int64(cap))
+            if st != AIR_ERR_CAPACITY:
+                break
+            cap = max(int(im.n_rays), int(im.n_out), cap)
+        _check(st)
+        self._cap_hint = max(self._cap_hint, int(im.n_out))
+        self._raster_src = (int(base_res), int(max_level))
+        return self._result(im, out), spec[:, :int(im.n_out)]
 
     def raster(self, quantity="p", band=0, mode="bilinear", mem="device"):
         """air_render_raster: finest-level raster [(n0 2^Lm), (n0 2^Lm)] (index

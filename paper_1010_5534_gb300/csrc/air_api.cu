@@ -118,13 +118,17 @@ static cudaError_t regrow(T *&p, int64_t old_cap, int64_t cap, int64_t keep, int
   return cudaSuccess;
 }
 
-air_status ensure_nodes(air_grid *g, int64_t need, int64_t keep, int64_t bound) {
+air_status ensure_nodes(air_grid *g, int64_t need, int64_t keep, int64_t bound, bool with_I) {
   Workspace &w = g->ws;
-  const int nb = g->gv.n_bands;
+  const int nb = with_I ? g->gv.n_bands : -1;  // -1 tags arrays without intensities
   if (w.cap >= need && w.n_bands == nb) return AIR_OK;
   int64_t cap = std::max<int64_t>(need, std::min<int64_t>(bound, std::max<int64_t>(2 * w.cap, need + need / 2)));
   if (cap < need) cap = need;
-  if (w.n_bands != nb) keep = 0;
+  if (w.n_bands != nb) {
+    keep = 0;
+    if (w.I) cudaFree(w.I);
+    w.I = nullptr;
+  }
   cudaStream_t st = g->stream;
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = regrow(w.view, w.cap, cap, keep, 1, st);
@@ -133,7 +137,7 @@ air_status ensure_nodes(air_grid *g, int64_t need, int64_t keep, int64_t bound) 
   if (e == cudaSuccess) e = regrow(w.pj, w.cap, cap, keep, 1, st);
   if (e == cudaSuccess) e = regrow(w.child, w.cap, cap, keep, 1, st);
   if (e == cudaSuccess) e = regrow(w.N, w.cap, cap, keep, 1, st);
-  if (e == cudaSuccess) e = regrow(w.I, w.cap, cap, keep, nb, st);
+  if (e == cudaSuccess && with_I) e = regrow(w.I, w.cap, cap, keep, nb, st);
   if (e == cudaSuccess) e = regrow(w.p, w.cap, cap, keep, 1, st);
   if (e == cudaSuccess) e = regrow(w.steps, w.cap, cap, keep, 1, st);
   if (e == cudaSuccess) e = regrow(w.flag, w.cap, cap, keep, 1, st);
@@ -291,10 +295,32 @@ air_status render_fixed(air_grid *g, const air_view *view, int32_t res, int32_t 
   return AIR_OK;
 }
 
-air_status render_adaptive(air_grid *g, const air_view *view, const air_params *pr, air_image *im) {
+// Device address of page-locked host memory (NULL if p is not page-locked).
+static const float *host_locked(const float *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? (const float *)a.devicePointer : nullptr;
+}
+
+air_status render_adaptive(air_grid *g, const air_view *view, const air_params *pr, air_image *im,
+                           float *spectra, int64_t spectra_cap) {
   g->raster.ok = false;  // the workspace tree is about to change
   air_status s = check_image(im);
   if (s) return s;
+  const bool streamed = spectra != nullptr;
+  const float *spectra_dev = nullptr;
+  if (streamed) {
+    if (!pr || pr->include_interior != 1)
+      return set_error(AIR_ERR_ARG, "streamed spectra are indexed by node: include_interior must be 1");
+    if (im->intensity) return set_error(AIR_ERR_ARG, "with streamed spectra out->intensity must be NULL");
+    if (spectra_cap < 0) return set_error(AIR_ERR_ARG, "spectra_cap < 0");
+    if (!(spectra_dev = host_locked(spectra)))
+      return set_error(AIR_ERR_ARG, "spectra must be page-locked host memory (cudaHostAlloc / cudaHostRegister)");
+    g->last.valid = false;
+  }
   Camera cam;
   if ((s = make_camera(view, cam))) return s;
   if (!pr) return set_error(AIR_ERR_ARG, "params is NULL");
@@ -318,8 +344,51 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
 
   air_params key = *pr;
   key.include_interior = 0;
-  const bool cached = g->last.valid && !std::memcmp(&g->last.view, view, sizeof(air_view)) &&
+  const bool cached = !streamed && g->last.valid && !std::memcmp(&g->last.view, view, sizeof(air_view)) &&
                       !std::memcmp(&g->last.params, &key, sizeof(air_params));
+  SpectraWork &sp = g->spectra;
+  bool stage_used[2] = {false, false}, overflow = false;
+  int stage_k = 0;
+  if (streamed) {
+    if (!sp.copy) CU_TRY(cudaStreamCreateWithFlags(&sp.copy, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+      if (!sp.marched[k]) CU_TRY(cudaEventCreateWithFlags(&sp.marched[k], cudaEventDisableTiming));
+      if (!sp.copied[k]) CU_TRY(cudaEventCreateWithFlags(&sp.copied[k], cudaEventDisableTiming));
+    }
+  }
+  // Step ii on nodes [first, first + count): with streamed spectra the march
+  // writes them to staging buffer k, which the copy stream then moves to the
+  // host array while the next sweep proceeds; buffer k is reused only after
+  // its copy has finished.
+  auto march_nodes = [&](const TreeView &tv, RaySource src, const MarchTune &tune, int launches) -> air_status {
+    RayOut ro{tv.N, tv.I, tv.cap, tv.steps, tv.p};
+    const int k = stage_k;
+    if (streamed) {
+      if (stage_used[k]) CU_TRY(cudaStreamWaitEvent(g->stream, sp.copied[k], 0));
+      CU_TRY(ensure((void **)&sp.stage[k], &sp.stage_b[k], sizeof(float) * (size_t)nb * (size_t)src.count));
+      ro.I = sp.stage[k];
+      ro.stride = src.count;
+      ro.ioff = src.first;
+    }
+    CU_TRY(prof_open(g, AIR_PHASE_MARCH, launches));
+    CU_TRY(launch_march(g->gv, cam, src, ro, tune, g->stream));
+    CU_TRY(prof_close(g));
+    if (streamed) {
+      if (src.first + src.count <= spectra_cap) {
+        CU_TRY(cudaEventRecord(sp.marched[k], g->stream));
+        CU_TRY(cudaStreamWaitEvent(sp.copy, sp.marched[k], 0));
+        CU_TRY(cudaMemcpy2DAsync(spectra + src.first, sizeof(float) * (size_t)spectra_cap, sp.stage[k],
+                                 sizeof(float) * (size_t)src.count, sizeof(float) * (size_t)src.count,
+                                 (size_t)nb, cudaMemcpyDeviceToHost, sp.copy));
+        CU_TRY(cudaEventRecord(sp.copied[k], sp.copy));
+        stage_used[k] = true;
+      } else {
+        overflow = true;  // finish the tree; the caller retries with a larger array
+      }
+      stage_k ^= 1;
+    }
+    return AIR_OK;
+  };
   int64_t n = 0, n_refined = 0;
   int32_t sweeps = 0;
   TreeView t;
@@ -329,7 +398,7 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
   } else {
     g->last.valid = false;
     const int64_t nbase = (int64_t)n0 * n0;
-    if ((s = ensure_nodes(g, std::min<int64_t>(bound, std::max<int64_t>(4 * nbase, w.cap)), 0, bound))) return s;
+    if ((s = ensure_nodes(g, std::min<int64_t>(bound, std::max<int64_t>(4 * nbase, w.cap)), 0, bound, !streamed))) return s;
     t = w.tree(n0, Lm);
     const MarchTune tune = march_tune(g, pr->fp64_level);
     g->prof.used = 0;
@@ -342,10 +411,7 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
     CU_TRY(cudaMemsetAsync(w.d_err, 0, sizeof(uint32_t), st));
     RaySource src{};
     src.mode = 0; src.n0 = n0; src.lvl = t.lvl; src.pi = t.pi; src.pj = t.pj; src.first = 0; src.count = nbase;
-    RayOut ro{t.N, t.I, t.cap, t.steps, t.p};
-    CU_TRY(prof_open(g, AIR_PHASE_MARCH, march_launches));
-    CU_TRY(launch_march(g->gv, cam, src, ro, tune, st));
-    CU_TRY(prof_close(g));
+    if ((s = march_nodes(t, src, tune, march_launches))) return s;
     n = nbase;
     for (;;) {
       // step iii: scan, then balance; count the flags
@@ -365,7 +431,7 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
       const int64_t n_new = n + 4 * nflag;
       if (n_new > bound) return set_error(AIR_ERR_NUMERIC, "quadtree exceeds its bound (%lld > %lld)", (long long)n_new, (long long)bound);
       if (n_new > w.cap) {
-        if ((s = ensure_nodes(g, n_new, n, bound))) return s;
+        if ((s = ensure_nodes(g, n_new, n, bound, !streamed))) return s;
         t = w.tree(n0, Lm);
         // the per-block offsets were computed for n items; they stay valid
       }
@@ -374,10 +440,7 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
       CU_TRY(launch_emit_children(t, w.flag, n, w.boff, n, st));
       CU_TRY(prof_close(g));
       src.lvl = t.lvl; src.pi = t.pi; src.pj = t.pj; src.first = n; src.count = 4 * nflag;
-      ro = RayOut{t.N, t.I, t.cap, t.steps, t.p};
-      CU_TRY(prof_open(g, AIR_PHASE_MARCH, march_launches));
-      CU_TRY(launch_march(g->gv, cam, src, ro, tune, st));
-      CU_TRY(prof_close(g));
+      if ((s = march_nodes(t, src, tune, march_launches))) return s;
       n = n_new;
       n_refined += nflag;
       ++sweeps;
@@ -389,11 +452,24 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
     g->last.params = key;
     g->last.n_nodes = n; g->last.n_refined = n_refined; g->last.n_sweeps = sweeps;
   }
-  return output_tree(g, cam, pr, im, n, n_refined, sweeps);
+  if (!streamed) return output_tree(g, cam, pr, im, n, n_refined, sweeps);
+  // the copies of the last sweeps must land before the flux reads the host array
+  for (int k = 0; k < 2; ++k)
+    if (stage_used[k]) CU_TRY(cudaStreamWaitEvent(st, sp.copied[k], 0));
+  if (overflow) {
+    CU_TRY(cudaStreamSynchronize(st));
+    im->n_out = n; im->n_leaves = (int64_t)n0 * n0 + 3 * n_refined; im->n_rays = n; im->n_sweeps = sweeps;
+    g->last.valid = false;
+    return set_error(AIR_ERR_CAPACITY, "spectra_cap %lld < %lld traced nodes", (long long)spectra_cap, (long long)n);
+  }
+  s = output_tree(g, cam, pr, im, n, n_refined, sweeps, spectra_dev, spectra_cap);
+  g->last.valid = false;  // the tree holds no intensities: no reuse by another render
+  return s;
 }
 
 air_status output_tree(air_grid *g, const Camera &cam, const air_params *pr, air_image *im,
-                       int64_t n, int64_t n_refined, int32_t sweeps) {
+                       int64_t n, int64_t n_refined, int32_t sweeps, const float *spectra_dev,
+                       int64_t spectra_cap) {
   air_status s = AIR_OK;
   Workspace &w = g->ws;
   const int nb = g->gv.n_bands;
@@ -416,7 +492,9 @@ air_status output_tree(air_grid *g, const Camera &cam, const air_params *pr, air
   g->raster.Lm = pr->max_level;
   CU_TRY(ensure((void **)&w.partial, &w.partial_b, sizeof(double) * (nb + 1) * flux_blocks(n)));
   FluxArgs fa{};
-  fa.n = n; fa.child = t.child; fa.lvl = t.lvl; fa.I = t.I; fa.stride = t.cap; fa.steps = t.steps;
+  fa.n = n; fa.child = t.child; fa.lvl = t.lvl; fa.steps = t.steps;
+  fa.I = spectra_dev ? spectra_dev : t.I;
+  fa.stride = spectra_dev ? spectra_cap : t.cap;
   fa.n_bands = nb; fa.area0 = (2.0 * cam.H / n0) * (2.0 * cam.H / n0); fa.partial = w.partial;
   OutView o;
   if ((s = out_view(g, im, n_out, o))) return s;
@@ -473,6 +551,14 @@ air_status air_render_adaptive(air_grid *g, const air_view *view, const air_para
   air::g_err[0] = 0;
   if (!g) return air::set_error(AIR_ERR_ARG, "grid is NULL");
   return air::render_adaptive(g, view, params, out);
+}
+
+air_status air_render_adaptive_spectra(air_grid *g, const air_view *view, const air_params *params,
+                                       air_image *out, float *spectra, int64_t spectra_cap) {
+  air::g_err[0] = 0;
+  if (!g) return air::set_error(AIR_ERR_ARG, "grid is NULL");
+  if (!spectra) return air::set_error(AIR_ERR_ARG, "spectra is NULL");
+  return air::render_adaptive(g, view, params, out, spectra, spectra_cap);
 }
 
 air_status air_profile_enable(air_grid *g, int32_t on) {

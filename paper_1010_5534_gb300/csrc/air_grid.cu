@@ -173,6 +173,19 @@ void free_grid_impl(air_grid *g) {
   dfree(g->d_table); dfree(g->d_kappa); dfree(g->d_invkappa);
   dfree(g->raster.scratch);
   g->raster.ok = false;
+  {
+    SpectraWork &sp = g->spectra;
+    if (sp.copy) cudaStreamSynchronize(sp.copy);
+    for (int k = 0; k < 2; ++k) {
+      dfree(sp.stage[k]);
+      sp.stage_b[k] = 0;
+      if (sp.marched[k]) cudaEventDestroy(sp.marched[k]);
+      if (sp.copied[k]) cudaEventDestroy(sp.copied[k]);
+      sp.marched[k] = sp.copied[k] = nullptr;
+    }
+    if (sp.copy) cudaStreamDestroy(sp.copy);
+    sp.copy = nullptr;
+  }
   free_batch(g);
   free_learn(g);
   Workspace &w = g->ws;

@@ -132,6 +132,17 @@ struct LearnWork {
          pp_b = 0, psteps_b = 0, missing_b = 0, counters_b = 0;
 };
 
+// Streamed spectra (air_render_adaptive_spectra): two device staging buffers
+// that take turns holding one sweep's spectra while a copy stream moves the
+// other to the caller's page-locked host array.
+struct SpectraWork {
+  cudaStream_t copy = nullptr;
+  cudaEvent_t marched[2] = {nullptr, nullptr};  // staging k written (compute stream)
+  cudaEvent_t copied[2] = {nullptr, nullptr};   // staging k free again (copy stream)
+  float *stage[2] = {nullptr, nullptr};
+  size_t stage_b[2] = {0, 0};
+};
+
 // The single-view tree that air_render_raster reads (set by output_tree).
 struct RasterSrc {
   bool ok = false;
@@ -162,6 +173,7 @@ struct air_grid {
   air::Workspace ws;
   air::LastRender last;
   air::RasterSrc raster;
+  air::SpectraWork spectra;
   air::Profiler prof;
   air::BatchWork batch;
   air::LearnWork learn;
@@ -181,13 +193,19 @@ void free_batch(air_grid *g);
 air_status check_image(const air_image *im);
 air_status make_camera(const air_view *v, Camera &c);
 air_status init_scalars(Workspace &w);
-air_status ensure_nodes(air_grid *g, int64_t need, int64_t keep, int64_t bound);
+// Node arrays for `need` nodes (the first `keep` preserved); with_I = false
+// leaves out the per-band intensities (streamed spectra keep them elsewhere).
+air_status ensure_nodes(air_grid *g, int64_t need, int64_t keep, int64_t bound, bool with_I = true);
 air_status render_batch(air_grid *g, const air_view *views, int32_t n_views,
                         const air_params *params, const air_batch_opts *opts, air_image *outs);
-air_status render_adaptive(air_grid *g, const air_view *view, const air_params *pr, air_image *im);
-// Step vi on the quadtree of nodes [0, n) in the workspace.
+// spectra (page-locked host, [n_bands][spectra_cap]) set: streamed spectra.
+air_status render_adaptive(air_grid *g, const air_view *view, const air_params *pr, air_image *im,
+                           float *spectra = nullptr, int64_t spectra_cap = 0);
+// Step vi on the quadtree of nodes [0, n) in the workspace; with spectra_dev
+// set, the band intensities are read from there (stride spectra_cap).
 air_status output_tree(air_grid *g, const Camera &cam, const air_params *pr, air_image *im,
-                       int64_t n, int64_t n_refined, int32_t sweeps);
+                       int64_t n, int64_t n_refined, int32_t sweeps,
+                       const float *spectra_dev = nullptr, int64_t spectra_cap = 0);
 air_status mlp_forward(air_mlp *m, const uint16_t *x, int64_t n, float *logits, cudaStream_t st);
 // The march configuration of this handle's tuning.
 MarchTune march_tune(const air_grid *g, int fp64_level);

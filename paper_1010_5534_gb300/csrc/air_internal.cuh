@@ -69,6 +69,8 @@ struct RayOut {
   float *p;             // [stride] band-summed intensity (NULL: written elsewhere)
   float *tau0;          // [stride] optical depth of band 0 through the grid (optional)
   uint8_t *maxlev;      // [stride] deepest brick level the ray crossed (optional)
+  int64_t ioff;         // node k's intensities sit at I[b * stride + k - ioff] (a
+                        // staging buffer for the nodes from ioff on; 0 otherwise)
 };
 
 struct MarchTune {
@@ -108,6 +110,6 @@ struct DeviceGrid;  // owned by the handle (defined in air_grid.cu)
 cudaError_t launch_march(const GridView &g, const Camera &cam, const RaySource &src,
                          const RayOut &out, const MarchTune &tune, cudaStream_t st);
 cudaError_t launch_band_sum(const float *I, int n_bands, int64_t stride, int64_t first,
-                            int64_t count, float *p, cudaStream_t st);
+                            int64_t count, float *p, cudaStream_t st, int64_t ioff = 0);
 
 }  // namespace air

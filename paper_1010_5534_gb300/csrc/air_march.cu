@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kMarchBlock, MinBlocks<NBT>::value)
   }
 #pragma unroll
   for (int b = 0; b < NBT; ++b)
-    if (b < nbh) out.I[(int64_t)(b0 + b) * out.stride + k] = st.I[b];
+    if (b < nbh) out.I[(int64_t)(b0 + b) * out.stride + (k - out.ioff)] = st.I[b];
   if (out.p && gridDim.y == 1) {
     float p = 0.f;
 #pragma unroll
@@ -72,12 +72,13 @@ __global__ void __launch_bounds__(kMarchBlock, MinBlocks<NBT>::value)
 }
 
 __global__ void k_band_sum(const float *__restrict__ I, int n_bands, int64_t stride, int64_t first,
-                           int64_t count, const int32_t *__restrict__ list, float *__restrict__ p) {
+                           int64_t count, const int32_t *__restrict__ list, float *__restrict__ p,
+                           int64_t ioff) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= count) return;
   const int64_t k = list ? (int64_t)list[r] : first + r;
   float s = 0.f;
-  for (int b = 0; b < n_bands; ++b) s += I[(int64_t)b * stride + k];
+  for (int b = 0; b < n_bands; ++b) s += I[(int64_t)b * stride + (k - ioff)];
   p[k] = s;
 }
 
@@ -120,10 +121,10 @@ static cudaError_t launch_t(const GridView &g, const Camera &cam, const RaySourc
     const int64_t count = src.mode == 0 ? src.count : (int64_t)src.n0 * src.n0;
     if (src.list) {
       k_band_sum<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(out.I, g.n_bands, out.stride, 0,
-                                                                  count, src.list, out.p);
+                                                                  count, src.list, out.p, out.ioff);
       return cudaGetLastError();
     }
-    return launch_band_sum(out.I, g.n_bands, out.stride, first, count, out.p, st);
+    return launch_band_sum(out.I, g.n_bands, out.stride, first, count, out.p, st, out.ioff);
   }
   return cudaSuccess;
 }
@@ -141,11 +142,11 @@ cudaError_t launch_march(const GridView &g, const Camera &cam, const RaySource &
 }
 
 cudaError_t launch_band_sum(const float *I, int n_bands, int64_t stride, int64_t first,
-                            int64_t count, float *p, cudaStream_t st) {
+                            int64_t count, float *p, cudaStream_t st, int64_t ioff) {
   if (count <= 0) return cudaSuccess;
   const int block = 256;
   k_band_sum<<<(unsigned)((count + block - 1) / block), block, 0, st>>>(I, n_bands, stride, first,
-                                                                       count, nullptr, p);
+                                                                       count, nullptr, p, ioff);
   return cudaGetLastError();
 }
 

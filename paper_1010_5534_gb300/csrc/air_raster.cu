@@ -60,6 +60,8 @@ air_status render_raster(air_grid *g, int32_t quantity, int32_t band, int32_t mo
   if (!g->raster.ok) return set_error(AIR_ERR_ARG, "no single-view adaptive image to rasterise");
   if (quantity == AIR_RASTER_INTENSITY && (band < 0 || band >= g->gv.n_bands))
     return set_error(AIR_ERR_ARG, "band %d out of range", band);
+  if (quantity == AIR_RASTER_INTENSITY && !g->ws.I)
+    return set_error(AIR_ERR_ARG, "the image's band intensities were streamed to host memory");
   const int n0 = g->raster.n0, Lm = g->raster.Lm;
   const int64_t nf = (int64_t)n0 << Lm;
   if (nf > (1 << 30)) return set_error(AIR_ERR_ARG, "raster side %lld too large", (long long)nf);
