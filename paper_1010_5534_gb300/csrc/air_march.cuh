@@ -313,11 +313,12 @@ __device__ __forceinline__ double exp2_neg(int L) {
 // 1/h and one residual correction), so a pixel centre that lies exactly on a
 // cell face maps exactly onto it, and the half-open rule picks the higher cell.
 __device__ __forceinline__ bool ray_setup(const GridView &g, const RayGeom &rg, int L, int i,
-                                          int j, double O[3], double &t0) {
+                                          int j, double O[3], double &t0, int &eax) {
   const double pix = rg.pix0 * exp2_neg(L);
   const double uc = fma((double)i + 0.5, pix, -rg.H);
   const double vc = fma((double)j + 0.5, pix, -rg.H);
   t0 = -DBL_MAX;
+  eax = -1;
   double t1 = DBL_MAX;
   bool hit = true;
 #pragma unroll
@@ -334,7 +335,10 @@ __device__ __forceinline__ bool ray_setup(const GridView &g, const RayGeom &rg, 
         ta = tb;
         tb = y;
       }
-      t0 = fmax(t0, ta);
+      if (ta > t0) {
+        t0 = ta;
+        eax = a;  // the box face the ray enters through
+      }
       t1 = fmin(t1, tb);
     }
   }
@@ -433,8 +437,8 @@ __device__ __forceinline__ int brick_of(const GridView &g, int e, const int c[3]
 // kernel-parameter bank, not held per thread.
 template <int NBT, int FMT>
 __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
-                          const RayGeom &rg, double t0, int fp64_level, const BandCtx &bc,
-                          const BandRegs<NBT> &br) {
+                          const RayGeom &rg, double t0, int eax, int fp64_level,
+                          const BandCtx &bc, const BandRegs<NBT> &br) {
   const int B = g.B, lb = g.log2B, Lm = g.Lm;
   const double *D = rg.D, *invD = rg.invD;
   F2 Of[3];
@@ -472,12 +476,22 @@ __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
     float tend = FLT_MAX;
     int ax = -1;
     double te = 0.0;
+    // On the axis the brick is entered through, the entry point is the face
+    // itself, an integer finest coordinate: its offset is exact. On an axis
+    // the ray does not move along, the offset O - anchor is constant and exact
+    // in double-float. Only the other axes need the FP64 (or double-float)
+    // position of the entry point.
     if (deep) {
       const double td = (double)t.hi + (double)t.lo;
       double tmin = DBL_MAX;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        Q[a] = (float)(fma(td, D[a], O[a] - (double)anchor[a]) * (double)scale);
+        if (a == eax)
+          Q[a] = (float)((Dl[a] > 0.f ? c[a] : c[a] + 1) - anchor[a]) * scale;
+        else if (Dl[a] == 0.f)
+          Q[a] = ((Of[a].hi - (float)anchor[a]) + Of[a].lo) * scale;
+        else
+          Q[a] = (float)fma(td, D[a], O[a] - (double)anchor[a]) * scale;
         if (Dl[a] != 0.f) {
           const double face = (double)(Dl[a] > 0.f ? bo[a] + S : bo[a]);
           const double ta = (face - O[a]) * invD[a];
@@ -495,7 +509,12 @@ __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
         F2 Dv;
         Dv.hi = rg.Dhi[a];
         Dv.lo = rg.Dlo[a];
-        Q[a] = f2_offset(Of[a], t, Dv, (float)anchor[a]) * scale;
+        if (a == eax)
+          Q[a] = (float)((Dl[a] > 0.f ? c[a] : c[a] + 1) - anchor[a]) * scale;
+        else if (Dl[a] == 0.f)
+          Q[a] = ((Of[a].hi - (float)anchor[a]) + Of[a].lo) * scale;
+        else
+          Q[a] = f2_offset(Of[a], t, Dv, (float)anchor[a]) * scale;
         if (Dl[a] != 0.f) {
           const float face = Dl[a] > 0.f ? (float)(B - lc[a]) : (float)(-lc[a]);
           const float ta = (face - Q[a]) * inv[a];
@@ -536,6 +555,7 @@ __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
     c[1] = cn[1];
     c[2] = cn[2];
     e = en;
+    eax = ax;
   }
 }
 
@@ -546,9 +566,10 @@ __device__ __forceinline__ void trace_ray(RTState<NBT> &st, const GridView &g, c
                                           const BandRegs<NBT> &br) {
   rt_init<NBT>(st);
   double O[3], t0;
-  if (ray_setup(g, rg, L, i, j, O, t0)) {
+  int eax;
+  if (ray_setup(g, rg, L, i, j, O, t0, eax)) {
     if (AMR)
-      march_amr<NBT, FMT>(st, g, O, rg, t0, fp64_level, bc, br);
+      march_amr<NBT, FMT>(st, g, O, rg, t0, eax, fp64_level, bc, br);
     else
       march_uniform<NBT, FMT>(st, g, O, rg, t0, bc, br);
   }
