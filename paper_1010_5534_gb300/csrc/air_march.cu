@@ -3,15 +3,19 @@
 
 namespace air {
 
-template <int NBT>
+// Resident blocks per SM for the one-band kernel of rays parallel to an axis.
+constexpr int kAxisBlocks = 14;
+
+template <int NBT, int DIR>
 struct MinBlocks {
-  static constexpr int value = NBT <= 1 ? 8 : (NBT <= 2 ? 5 : (NBT <= 4 ? 4 : (NBT <= 8 ? 3 : 2)));
+  static constexpr int value = DIR == 1 ? kAxisBlocks
+                               : (NBT <= 1 ? 8 : (NBT <= 2 ? 5 : (NBT <= 4 ? 4 : (NBT <= 8 ? 3 : 2))));
 };
 
 constexpr int kMarchBlock = 128;
 
-template <int NBT, bool AMR, int FMT>
-__global__ void __launch_bounds__(kMarchBlock, MinBlocks<NBT>::value)
+template <int NBT, bool AMR, int FMT, int DIR>
+__global__ void __launch_bounds__(kMarchBlock, MinBlocks<NBT, DIR>::value)
     k_march(GridView g, RayGeom rg, RaySource src, RayOut out, int fp64_level) {
   extern __shared__ float smem[];
   const int chunk = blockIdx.y;
@@ -52,7 +56,7 @@ __global__ void __launch_bounds__(kMarchBlock, MinBlocks<NBT>::value)
     L = 0;
   }
   RTState<NBT> st;
-  trace_ray<NBT, AMR, FMT>(st, g, rg, L, i, j, fp64_level, bc, br);
+  trace_ray<NBT, AMR, FMT, DIR>(st, g, rg, L, i, j, fp64_level, bc, br);
   if (chunk == 0) {
     out.N[k] = st.N;
     out.steps[k] = st.steps;
@@ -102,18 +106,24 @@ static cudaError_t launch_t(const GridView &g, const Camera &cam, const RaySourc
   const RayGeom rg = make_geom(g, cam, src.n0);
   dim3 grid((unsigned)blocks, chunks);
   const bool amr = g.kind == AIR_GRID_AMR;
-  if (g.cell_fmt == kCellRho) {
-    if (amr) k_march<NBT, true, kCellRho><<<grid, block, smem, st>>>(g, rg, src, out, tune.fp64_level);
-    else k_march<NBT, false, kCellRho><<<grid, block, smem, st>>>(g, rg, src, out, tune.fp64_level);
+  const int moving = (rg.Dhi[0] != 0.f) + (rg.Dhi[1] != 0.f) + (rg.Dhi[2] != 0.f);
+  const int fp = tune.fp64_level;
+#define AIR_MARCH(N, A, F, D) k_march<N, A, F, D><<<grid, block, smem, st>>>(g, rg, src, out, fp)
+  if (NBT == 1 && moving == 1) {
+    // every ray parallel to one grid axis
+    if (g.cell_fmt == kCellRho) { if (amr) AIR_MARCH(1, true, kCellRho, 1); else AIR_MARCH(1, false, kCellRho, 1); }
+    else if (g.cell_fmt == kCellXq) { if (amr) AIR_MARCH(1, true, kCellXq, 1); else AIR_MARCH(1, false, kCellXq, 1); }
+    else { if (amr) AIR_MARCH(1, true, kCellLam, 1); else AIR_MARCH(1, false, kCellLam, 1); }
+  } else if (g.cell_fmt == kCellRho) {
+    if (amr) AIR_MARCH(NBT, true, kCellRho, 0); else AIR_MARCH(NBT, false, kCellRho, 0);
   } else if (g.cell_fmt == kCellXq) {
-    if (amr) k_march<NBT, true, kCellXq><<<grid, block, smem, st>>>(g, rg, src, out, tune.fp64_level);
-    else k_march<NBT, false, kCellXq><<<grid, block, smem, st>>>(g, rg, src, out, tune.fp64_level);
+    if (amr) AIR_MARCH(NBT, true, kCellXq, 0); else AIR_MARCH(NBT, false, kCellXq, 0);
   } else {
     // per-cell Lambda exists for one-band grids only
     if (NBT != 1) return cudaErrorInvalidValue;
-    if (amr) k_march<1, true, kCellLam><<<grid, block, smem, st>>>(g, rg, src, out, tune.fp64_level);
-    else k_march<1, false, kCellLam><<<grid, block, smem, st>>>(g, rg, src, out, tune.fp64_level);
+    if (amr) AIR_MARCH(1, true, kCellLam, 0); else AIR_MARCH(1, false, kCellLam, 0);
   }
+#undef AIR_MARCH
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (chunks > 1 && out.p) {

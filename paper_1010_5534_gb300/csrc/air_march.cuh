@@ -177,13 +177,16 @@ __device__ __forceinline__ void prefetch_cell(const void *__restrict__ cells, Id
 // a grid axis takes a one-axis form of the same loop (one boundary parameter,
 // one counter, one bound); the per-launch direction makes this choice the
 // same for every thread.
-template <int NBT, int FMT, typename Idx>
+// DIR = 1: the launch's rays are all parallel to one grid axis, so only the
+// one-axis form is compiled (fewer registers, more resident warps); DIR = 0
+// chooses between the two forms at run time.
+template <int NBT, int FMT, typename Idx, int DIR = 0>
 __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], const float Dl[3],
                                             const float inv[3], float tend, int lx, int ly, int lz,
                                             int nx, int ny, int nz, Idx sy, Idx sz,
                                             const void *__restrict__ cells, const BandCtx &bc,
                                             const BandRegs<NBT> &br) {
-  if (Dl[0] == 0.f ? (Dl[1] == 0.f) != (Dl[2] == 0.f) : (Dl[1] == 0.f && Dl[2] == 0.f)) {
+  if (DIR == 1 || (Dl[0] == 0.f ? (Dl[1] == 0.f) != (Dl[2] == 0.f) : (Dl[1] == 0.f && Dl[2] == 0.f))) {
     // the ray is parallel to one grid axis (a face-on view): a one-axis DDA
     const int ax = Dl[0] != 0.f ? 0 : (Dl[1] != 0.f ? 1 : 2);
     const float D1 = ax == 0 ? Dl[0] : (ax == 1 ? Dl[1] : Dl[2]);
@@ -230,6 +233,7 @@ __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], c
     }
     return;
   }
+  if constexpr (DIR != 1) {
   const float INF = FLT_MAX;
   const bool p0 = Dl[0] > 0.f, p1 = Dl[1] > 0.f, p2 = Dl[2] > 0.f;
   const float a0 = fabsf(inv[0]), a1 = fabsf(inv[1]), a2 = fabsf(inv[2]);
@@ -285,6 +289,7 @@ __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], c
     if (!more) break;  // left the block (through its far face, or by rounding)
     rh = rh_n;
     xv = xv_n;
+  }
   }
 }
 
@@ -347,7 +352,7 @@ __device__ __forceinline__ bool ray_setup(const GridView &g, const RayGeom &rg, 
 
 __device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
 
-template <int NBT, int FMT>
+template <int NBT, int FMT, int DIR = 0>
 __device__ void march_uniform(RTState<NBT> &r, const GridView &g, const double O[3],
                               const RayGeom &rg, double t0, const BandCtx &bc,
                               const BandRegs<NBT> &br) {
@@ -362,7 +367,7 @@ __device__ void march_uniform(RTState<NBT> &r, const GridView &g, const double O
     inv[a] = rg.invDhi[a];
   }
   // the ray leaves through a face of the grid: no end parameter needed
-  march_block<NBT, FMT, int64_t>(r, Q, Dl, inv, FLT_MAX, lc[0], lc[1], lc[2], g.nf[0], g.nf[1],
+  march_block<NBT, FMT, int64_t, DIR>(r, Q, Dl, inv, FLT_MAX, lc[0], lc[1], lc[2], g.nf[0], g.nf[1],
                                  g.nf[2], (int64_t)g.nf[0], (int64_t)g.nf[0] * g.nf[1], g.cells,
                                  bc, br);
 }
@@ -435,7 +440,7 @@ __device__ __forceinline__ int brick_of(const GridView &g, int e, const int c[3]
 // is marched, so its latency overlaps the march. Per-launch constants
 // (direction, its inverse and its double-float split) are read from the
 // kernel-parameter bank, not held per thread.
-template <int NBT, int FMT>
+template <int NBT, int FMT, int DIR = 0>
 __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
                           const RayGeom &rg, double t0, int eax, int fp64_level,
                           const BandCtx &bc, const BandRegs<NBT> &br) {
@@ -545,7 +550,7 @@ __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
     const int64_t boff = (int64_t)code << (3 * lb);
     const void *cb = FMT == kCellRho ? (const void *)((const float *)g.cells + boff)
                                      : (const void *)((const uint2 *)g.cells + boff);
-    march_block<NBT, FMT, int>(r, Q, Dl, inv, tend, lc[0], lc[1], lc[2], B, B, B, B, B * B, cb,
+    march_block<NBT, FMT, int, DIR>(r, Q, Dl, inv, tend, lc[0], lc[1], lc[2], B, B, B, B, B * B, cb,
                                bc, br);
     if (out) break;
     // advance to the exit point
@@ -560,7 +565,7 @@ __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
 }
 
 // One ray (pixel (L, i, j)) through the grid, bands [b0, b0 + NBT) of bc/br.
-template <int NBT, bool AMR, int FMT>
+template <int NBT, bool AMR, int FMT, int DIR = 0>
 __device__ __forceinline__ void trace_ray(RTState<NBT> &st, const GridView &g, const RayGeom &rg,
                                           int L, int i, int j, int fp64_level, const BandCtx &bc,
                                           const BandRegs<NBT> &br) {
@@ -569,9 +574,9 @@ __device__ __forceinline__ void trace_ray(RTState<NBT> &st, const GridView &g, c
   int eax;
   if (ray_setup(g, rg, L, i, j, O, t0, eax)) {
     if (AMR)
-      march_amr<NBT, FMT>(st, g, O, rg, t0, eax, fp64_level, bc, br);
+      march_amr<NBT, FMT, DIR>(st, g, O, rg, t0, eax, fp64_level, bc, br);
     else
-      march_uniform<NBT, FMT>(st, g, O, rg, t0, bc, br);
+      march_uniform<NBT, FMT, DIR>(st, g, O, rg, t0, bc, br);
   }
 }
 
