@@ -8,7 +8,7 @@ constexpr int kAxisBlocks = 14;
 
 template <int NBT, int DIR>
 struct MinBlocks {
-  static constexpr int value = DIR == 1 ? kAxisBlocks
+  static constexpr int value = DIR >= 1 ? kAxisBlocks
                                : (NBT <= 1 ? 8 : (NBT <= 2 ? 5 : (NBT <= 4 ? 4 : (NBT <= 8 ? 3 : 2))));
 };
 
@@ -110,10 +110,16 @@ static cudaError_t launch_t(const GridView &g, const Camera &cam, const RaySourc
   const int fp = tune.fp64_level;
 #define AIR_MARCH(N, A, F, D) k_march<N, A, F, D><<<grid, block, smem, st>>>(g, rg, src, out, fp)
   if (NBT == 1 && moving == 1) {
-    // every ray parallel to one grid axis
-    if (g.cell_fmt == kCellRho) { if (amr) AIR_MARCH(1, true, kCellRho, 1); else AIR_MARCH(1, false, kCellRho, 1); }
-    else if (g.cell_fmt == kCellXq) { if (amr) AIR_MARCH(1, true, kCellXq, 1); else AIR_MARCH(1, false, kCellXq, 1); }
-    else { if (amr) AIR_MARCH(1, true, kCellLam, 1); else AIR_MARCH(1, false, kCellLam, 1); }
+    // every ray parallel to grid axis A: DIR = 1 + A
+    const int A = rg.Dhi[0] != 0.f ? 0 : (rg.Dhi[1] != 0.f ? 1 : 2);
+#define AIR_AXIS(D)                                                                              \
+  if (g.cell_fmt == kCellRho) { if (amr) AIR_MARCH(1, true, kCellRho, D); else AIR_MARCH(1, false, kCellRho, D); } \
+  else if (g.cell_fmt == kCellXq) { if (amr) AIR_MARCH(1, true, kCellXq, D); else AIR_MARCH(1, false, kCellXq, D); } \
+  else { if (amr) AIR_MARCH(1, true, kCellLam, D); else AIR_MARCH(1, false, kCellLam, D); }
+    if (A == 0) { AIR_AXIS(1) }
+    else if (A == 1) { AIR_AXIS(2) }
+    else { AIR_AXIS(3) }
+#undef AIR_AXIS
   } else if (g.cell_fmt == kCellRho) {
     if (amr) AIR_MARCH(NBT, true, kCellRho, 0); else AIR_MARCH(NBT, false, kCellRho, 0);
   } else if (g.cell_fmt == kCellXq) {

@@ -109,3 +109,22 @@ def test_batch_bounded_wait_returns_timeout(cone):
     b = g.render_batch(vs, 8, 2, 0.5)
     s = g.render_adaptive(vs[1], 8, 2, 0.5)
     same(b[1], s, "after timeout")
+
+
+def test_batch_equals_single_views_one_band():
+    """One-band grid: a single-view render of a face-on view runs the compiled
+    one-axis march kernel, the batched kernel the general form with its
+    run-time choice of the one-axis loop; the bits must agree."""
+    s = scenes.cone_shock_amr(5, n_base=32, brick=8, levels=2, thickness=0.08)
+    g = air.Grid(s)
+    vs = [scenes.axis_view(a) for a in ("+z", "-x", "+y")] + scenes.random_views(22, 1)
+    singles = [g.render_adaptive(v, 16, 3, 0.3, include_interior=True) for v in vs]
+    batch = g.render_batch(vs, 16, 3, 0.3, include_interior=True)
+    for k, (a, b) in enumerate(zip(batch, singles)):
+        same(a, b, f"one-band view {k}")
+    for v in vs[:3]:   # fixed images too (one-axis kernel) against the same rays in a batch base image
+        f = g.render_fixed(v, 16)
+        b = g.render_batch([v], 16, 0, 0.3, include_interior=True)[0]
+        assert (np_(f["coldens"]) == np_(b["coldens"])).all()
+        assert (np_(f["intensity"]) == np_(b["intensity"])).all()
+    g.close()
