@@ -17,6 +17,8 @@
 namespace air {
 
 // Step iii: flag every leaf below max_level whose xi >= xi_crit.
+// One thread per node (the FP64 work of the scanned leaves spreads over the
+// whole grid).
 __global__ void k_xi_scan(TreeView t, int64_t n, double xi_crit, int xi_norm, int refine_on,
                           uint32_t *__restrict__ flag) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -24,12 +26,15 @@ __global__ void k_xi_scan(TreeView t, int64_t n, double xi_crit, int xi_norm, in
   flag[k] = xi_flag(t, 0, k, xi_crit, xi_norm, refine_on);
 }
 
-// Step iii, balance closure from every flagged leaf.
+// Step iii, balance closure from every flagged leaf (the closure is a unique
+// fixed point, whatever order the threads reach it in). Grid-stride over the
+// nodes with a few blocks per SM: few nodes are flagged, so one thread per
+// node would spend the launch scheduling blocks that do nothing.
 __global__ void k_balance(TreeView t, int64_t n, uint32_t *__restrict__ flag,
                           uint32_t *__restrict__ err) {
-  const int64_t k0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k0 >= n || flag[k0] == 0) return;
-  balance_from(t, 0, (int)k0, flag, err);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k0 < n; k0 += stride)
+    if (flag[k0] != 0) balance_from(t, 0, (int)k0, flag, err);
 }
 
 // ---- warp-ballot prefix sums ------------------------------------------------
@@ -249,6 +254,21 @@ cudaError_t launch_init_base(const TreeView &t, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Blocks for a grid-stride launch: enough for `per_sm` blocks on every SM.
+static unsigned stride_blocks(int64_t n, int block, int per_sm) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+      cudaGetLastError();
+      sms = 1;
+    }
+  }
+  const int64_t cap = (int64_t)sms * per_sm;
+  const int64_t need = (n + block - 1) / block;
+  return (unsigned)(need < cap ? need : cap);
+}
+
 cudaError_t launch_xi_scan(const TreeView &t, int64_t n, double xi_crit, int xi_norm,
                            int refine_on, uint32_t *flag, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
@@ -259,7 +279,7 @@ cudaError_t launch_xi_scan(const TreeView &t, int64_t n, double xi_crit, int xi_
 cudaError_t launch_balance(const TreeView &t, int64_t n, uint32_t *flag, uint32_t *err,
                            cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_balance<<<nblk(n, 128), 128, 0, st>>>(t, n, flag, err);
+  k_balance<<<stride_blocks(n, 128, 16), 128, 0, st>>>(t, n, flag, err);
   return cudaGetLastError();
 }
 
