@@ -3,15 +3,12 @@
 
 namespace air {
 
-// Resident blocks per SM for the one-band kernels of rays parallel to an axis,
-// and of rays parallel to none.
+// Resident blocks per SM for the one-band kernel of rays parallel to an axis.
 constexpr int kAxisBlocks = 14;
-constexpr int kObliqueBlocks = 8;
 
 template <int NBT, int DIR>
 struct MinBlocks {
-  static constexpr int value = (DIR >= 1 && DIR <= 3) ? kAxisBlocks
-                               : (DIR == 4 && NBT <= 1) ? kObliqueBlocks
+  static constexpr int value = DIR >= 1 ? kAxisBlocks
                                : (NBT <= 1 ? 8 : (NBT <= 2 ? 5 : (NBT <= 4 ? 4 : (NBT <= 8 ? 3 : 2))));
 };
 
@@ -123,11 +120,6 @@ static cudaError_t launch_t(const GridView &g, const Camera &cam, const RaySourc
     else if (A == 1) { AIR_AXIS(2) }
     else { AIR_AXIS(3) }
 #undef AIR_AXIS
-  } else if (NBT == 1 && moving >= 2) {
-    // no ray parallel to an axis: the 3-axis form only
-    if (g.cell_fmt == kCellRho) { if (amr) AIR_MARCH(1, true, kCellRho, 4); else AIR_MARCH(1, false, kCellRho, 4); }
-    else if (g.cell_fmt == kCellXq) { if (amr) AIR_MARCH(1, true, kCellXq, 4); else AIR_MARCH(1, false, kCellXq, 4); }
-    else { if (amr) AIR_MARCH(1, true, kCellLam, 4); else AIR_MARCH(1, false, kCellLam, 4); }
   } else if (g.cell_fmt == kCellRho) {
     if (amr) AIR_MARCH(NBT, true, kCellRho, 0); else AIR_MARCH(NBT, false, kCellRho, 0);
   } else if (g.cell_fmt == kCellXq) {

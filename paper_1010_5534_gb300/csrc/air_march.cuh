@@ -178,17 +178,17 @@ __device__ __forceinline__ void prefetch_cell(const void *__restrict__ cells, Id
 // one counter, one bound); the per-launch direction makes this choice the
 // same for every thread.
 // DIR = 1 + A: the launch's rays are all parallel to grid axis A, so only the
-// one-axis form is compiled (fewer registers, more resident warps); DIR = 4:
-// no ray of the launch is parallel to an axis, only the 3-axis form; DIR = 0
-// chooses between the two forms at run time.
+// one-axis form is compiled (fewer registers, more resident warps); DIR = 0
+// chooses between the two forms at run time. (A 3-axis-only form was tried
+// for oblique launches: within 1% of DIR = 0 at 56 registers, and at 64 its
+// code ran twice as slow, so it is not kept.)
 template <int NBT, int FMT, typename Idx, int DIR = 0>
 __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], const float Dl[3],
                                             const float inv[3], float tend, int lx, int ly, int lz,
                                             int nx, int ny, int nz, Idx sy, Idx sz,
                                             const void *__restrict__ cells, const BandCtx &bc,
                                             const BandRegs<NBT> &br) {
-  if ((DIR >= 1 && DIR <= 3) ||
-      (DIR == 0 && (Dl[0] == 0.f ? (Dl[1] == 0.f) != (Dl[2] == 0.f) : (Dl[1] == 0.f && Dl[2] == 0.f)))) {
+  if (DIR >= 1 || (Dl[0] == 0.f ? (Dl[1] == 0.f) != (Dl[2] == 0.f) : (Dl[1] == 0.f && Dl[2] == 0.f))) {
     // the ray is parallel to one grid axis (a face-on view): a one-axis DDA
     const int ax = Dl[0] != 0.f ? 0 : (Dl[1] != 0.f ? 1 : 2);
     const float D1 = ax == 0 ? Dl[0] : (ax == 1 ? Dl[1] : Dl[2]);
@@ -235,7 +235,7 @@ __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], c
     }
     return;
   }
-  if constexpr (DIR == 0 || DIR == 4) {
+  if constexpr (DIR == 0) {
   const float INF = FLT_MAX;
   const bool p0 = Dl[0] > 0.f, p1 = Dl[1] > 0.f, p2 = Dl[2] > 0.f;
   const float a0 = fabsf(inv[0]), a1 = fabsf(inv[1]), a2 = fabsf(inv[2]);
@@ -655,7 +655,7 @@ __device__ __forceinline__ void trace_ray(RTState<NBT> &st, const GridView &g, c
   int eax;
   if (ray_setup(g, rg, L, i, j, O, t0, eax)) {
     if (AMR) {
-      if constexpr (DIR >= 1 && DIR <= 3)
+      if constexpr (DIR >= 1)
         march_amr_axis<NBT, FMT, DIR - 1>(st, g, O, rg, t0, fp64_level, bc, br);
       else
         march_amr<NBT, FMT, DIR>(st, g, O, rg, t0, eax, fp64_level, bc, br);
