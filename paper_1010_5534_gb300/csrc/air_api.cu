@@ -46,10 +46,10 @@ cudaError_t ensure(void **p, size_t *have, size_t bytes) {
   } while (0)
 
 air_status init_scalars(Workspace &w) {
-  if (!w.d_total) CU_TRY(cudaMalloc((void **)&w.d_total, sizeof(int64_t)));
+  if (!w.d_total) CU_TRY(cudaMalloc((void **)&w.d_total, 3 * sizeof(int64_t)));
   if (!w.d_err) CU_TRY(cudaMalloc((void **)&w.d_err, sizeof(uint32_t)));
   if (!w.d_flux) CU_TRY(cudaMalloc((void **)&w.d_flux, sizeof(double) * (kMaxBands + 1)));
-  if (!w.h_total) CU_TRY(cudaMallocHost((void **)&w.h_total, sizeof(int64_t)));
+  if (!w.h_total) CU_TRY(cudaMallocHost((void **)&w.h_total, 3 * sizeof(int64_t)));
   if (!w.h_err) CU_TRY(cudaMallocHost((void **)&w.h_err, sizeof(uint32_t)));
   if (!w.h_flux) CU_TRY(cudaMallocHost((void **)&w.h_flux, sizeof(double) * (kMaxBands + 1)));
   return AIR_OK;
@@ -362,8 +362,12 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
   for (int l = 0; l <= Lm; ++l) bound += ((int64_t)n0 << l) * ((int64_t)n0 << l);
   if (bound > INT32_MAX) return set_error(AIR_ERR_ARG, "image pyramid exceeds 2^31 nodes");
   // per-block scan offsets for any node count up to the bound (never resized mid-render)
-  CU_TRY(ensure((void **)&w.bcount, &w.bcount_b, sizeof(int32_t) * scan_blocks(bound)));
-  CU_TRY(ensure((void **)&w.boff, &w.boff_b, sizeof(int64_t) * scan_blocks(bound)));
+  CU_TRY(ensure((void **)&w.bcount, &w.bcount_b, 3 * sizeof(int32_t) * scan_blocks(bound)));
+  CU_TRY(ensure((void **)&w.boff, &w.boff_b, 3 * sizeof(int64_t) * scan_blocks(bound)));
+  // open-leaf lists: at most every node below the top level
+  const int64_t open_max = std::max<int64_t>(1, bound - ((int64_t)n0 << Lm) * ((int64_t)n0 << Lm));
+  for (int k = 0; k < 2; ++k)
+    CU_TRY(ensure((void **)&w.open[k], &w.open_b[k], sizeof(int32_t) * (size_t)open_max));
 
   air_params key = *pr;
   key.include_interior = 0;
@@ -436,20 +440,26 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
     src.mode = 0; src.n0 = n0; src.lvl = t.lvl; src.pi = t.pi; src.pj = t.pj; src.first = 0; src.count = nbase;
     if ((s = march_nodes(t, src, tune, march_launches))) return s;
     n = nbase;
+    // open-leaf list: the base pixels, unless the base is the top level
+    int cur = 0;
+    int64_t m = Lm > 0 ? nbase : 0;
+    CU_TRY(launch_list_init(w.open[0], m, st));
     for (;;) {
-      // step iii: scan, then balance; count the flags
+      if (m == 0) break;  // no leaf below the top level: nothing can be flagged
+      // step iii: scan, then balance; count the flags and the next list
       CU_TRY(prof_open(g, AIR_PHASE_SCAN, 1));
-      CU_TRY(launch_xi_scan(t, n, pr->xi_crit, pr->xi_norm, pr->refine_on, w.flag, st));
+      CU_TRY(launch_list_scan(t, w.open[cur], m, pr->xi_crit, pr->xi_norm, pr->refine_on, w.flag, st));
       CU_TRY(prof_close(g));
       CU_TRY(prof_open(g, AIR_PHASE_BALANCE, 1));
-      CU_TRY(launch_balance(t, n, w.flag, w.d_err, st));
+      CU_TRY(launch_list_balance(t, w.open[cur], m, w.flag, w.d_err, st));
       CU_TRY(prof_close(g));
       CU_TRY(prof_open(g, AIR_PHASE_REFINE, 2));
-      CU_TRY(launch_count_flags(w.flag, n, w.bcount, w.boff, w.d_total, st));
+      CU_TRY(launch_list_count(t, w.open[cur], m, w.flag, w.bcount, w.boff, w.d_total, st));
       CU_TRY(prof_close(g));
-      CU_TRY(cudaMemcpyAsync(w.h_total, w.d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+      CU_TRY(cudaMemcpyAsync(w.h_total, w.d_total, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
       CU_TRY(cudaStreamSynchronize(st));
-      const int64_t nflag = *w.h_total;
+      const int64_t nflag = w.h_total[0];
+      const int64_t m_next = w.h_total[1] + 4 * w.h_total[2];
       if (nflag == 0) break;
       const int64_t n_new = n + 4 * nflag;
       if (n_new > bound) return set_error(AIR_ERR_NUMERIC, "quadtree exceeds its bound (%lld > %lld)", (long long)n_new, (long long)bound);
@@ -458,15 +468,17 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
         t = w.tree(n0, Lm);
         // the per-block offsets were computed for n items; they stay valid
       }
-      // step iv: refine, then step ii on the new pixels
+      // step iv: refine (and the next open-leaf list), then step ii on the new pixels
       CU_TRY(prof_open(g, AIR_PHASE_REFINE, 1));
-      CU_TRY(launch_emit_children(t, w.flag, n, w.boff, n, st));
+      CU_TRY(launch_list_emit(t, w.open[cur], m, w.flag, w.boff, w.d_total, n, w.open[cur ^ 1], st));
       CU_TRY(prof_close(g));
       src.lvl = t.lvl; src.pi = t.pi; src.pj = t.pj; src.first = n; src.count = 4 * nflag;
       if ((s = march_nodes(t, src, tune, march_launches))) return s;
       n = n_new;
       n_refined += nflag;
       ++sweeps;
+      m = m_next;
+      cur ^= 1;
     }
     CU_TRY(cudaMemcpyAsync(w.h_err, w.d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CU_TRY(cudaStreamSynchronize(st));

@@ -27,7 +27,9 @@ struct Workspace {
   int32_t *bcount = nullptr;
   int64_t *boff = nullptr;
   size_t bcount_b = 0, boff_b = 0;
-  int64_t *d_total = nullptr;
+  int64_t *d_total = nullptr;  // [3]
+  int32_t *open[2] = {nullptr, nullptr};  // open-leaf lists (ping-pong)
+  size_t open_b[2] = {0, 0};
   uint32_t *d_err = nullptr;
   double *partial = nullptr;
   size_t partial_b = 0;
@@ -42,7 +44,7 @@ struct Workspace {
   float *o_N = nullptr, *o_p = nullptr, *o_I = nullptr;
   size_t o_level_b = 0, o_i_b = 0, o_j_b = 0, o_leaf_b = 0, o_N_b = 0, o_p_b = 0, o_I_b = 0;
   // pinned host scalars
-  int64_t *h_total = nullptr;
+  int64_t *h_total = nullptr;  // [3]
   uint32_t *h_err = nullptr;
   double *h_flux = nullptr;  // [kMaxBands + 1]
 

@@ -147,6 +147,170 @@ __global__ void __launch_bounds__(kScanBlock) k_emit_children(TreeView t, const 
   block_scan_emit(PredFlag{flag}, e, n, boff[blockIdx.x]);
 }
 
+// ---- open-leaf list -----------------------------------------------------------
+// The leaves below the top level, in ascending node order: the only nodes a
+// sweep can flag. Steps iii and iv run over this list instead of every node;
+// children are still emitted in parent (node) order, so the quadtree is the
+// same. Flags of nodes outside the list are kept at zero (a refined node's
+// flag is cleared when its children are emitted, children start at zero).
+
+__global__ void k_iota(int32_t *list, int64_t m) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) list[i] = (int32_t)i;
+}
+
+__global__ void k_xi_scan_list(TreeView t, const int32_t *__restrict__ open, int64_t m,
+                               double xi_crit, int xi_norm, int refine_on,
+                               uint32_t *__restrict__ flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int64_t k = open[i];
+  flag[k] = xi_flag(t, 0, k, xi_crit, xi_norm, refine_on);
+}
+
+__global__ void k_balance_list(TreeView t, const int32_t *__restrict__ open, int64_t m,
+                               uint32_t *__restrict__ flag, uint32_t *__restrict__ err) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    const int k = open[i];
+    if (flag[k] != 0) balance_from(t, 0, k, flag, err);
+  }
+}
+
+// Three selections over the list, per entry k = open[i]: flagged (refined
+// this sweep), kept (not flagged: stays an open leaf), and flagged with
+// children below the top level (its four children join the list).
+struct ListSel {
+  bool f, keep, co;
+};
+__device__ __forceinline__ ListSel list_sel(const TreeView &t, const int32_t *open, int64_t m,
+                                            const uint32_t *flag, int Lm, int64_t i, int &k) {
+  ListSel q{false, false, false};
+  k = 0;
+  if (i < m) {
+    k = open[i];
+    q.f = flag[k] != 0;
+    q.keep = !q.f;
+    q.co = q.f && t.lvl[k] + 1 < Lm;
+  }
+  return q;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_count3(TreeView t, const int32_t *open, int64_t m,
+                                                       const uint32_t *flag, int Lm,
+                                                       int32_t *bcount, int64_t nb) {
+  __shared__ int32_t wsum[3][kScanBlock / 32];
+  const int64_t start = (int64_t)blockIdx.x * kScanItems;
+  int32_t c0 = 0, c1 = 0, c2 = 0;
+  for (int rr = 0; rr < kScanRounds; ++rr) {
+    int k;
+    const ListSel q = list_sel(t, open, m, flag, Lm, start + (int64_t)rr * kScanBlock + threadIdx.x, k);
+    c0 += __popc(__ballot_sync(0xffffffffu, q.f));
+    c1 += __popc(__ballot_sync(0xffffffffu, q.keep));
+    c2 += __popc(__ballot_sync(0xffffffffu, q.co));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    wsum[0][threadIdx.x >> 5] = c0;
+    wsum[1][threadIdx.x >> 5] = c1;
+    wsum[2][threadIdx.x >> 5] = c2;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    int32_t s = 0;
+    for (int w = 0; w < kScanBlock / 32; ++w) s += wsum[threadIdx.x][w];
+    bcount[threadIdx.x * nb + blockIdx.x] = s;
+  }
+}
+
+// Block b of the launch scans selection b's per-block counts.
+__global__ void __launch_bounds__(1024) k_scan_blocks3(const int32_t *bcount, int64_t nb,
+                                                       int64_t *boff, int64_t *total) {
+  __shared__ int64_t part[1024];
+  const int32_t *bc = bcount + blockIdx.x * nb;
+  int64_t *bo = boff + blockIdx.x * nb;
+  const int64_t per = (nb + 1023) / 1024;
+  const int64_t a = threadIdx.x * per, b = min(nb, a + per);
+  int64_t s = 0;
+  for (int64_t x = a; x < b; ++x) s += bc[x];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const int64_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int64_t run = part[threadIdx.x] - s;
+  for (int64_t x = a; x < b; ++x) {
+    bo[x] = run;
+    run += bc[x];
+  }
+  if (threadIdx.x == 1023) total[blockIdx.x] = part[1023];
+}
+
+// Step iv over the list, and the next list: kept entries first (in order),
+// then the children below the top level (in order).
+__global__ void __launch_bounds__(kScanBlock) k_emit3(TreeView t, const int32_t *open, int64_t m,
+                                                      uint32_t *flag, int Lm, const int64_t *boff,
+                                                      const int64_t *total, int64_t nb,
+                                                      int64_t n_old, int32_t *next) {
+  __shared__ int32_t wsum[3][kScanBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t start = (int64_t)blockIdx.x * kScanItems;
+  int64_t run0 = boff[blockIdx.x], run1 = boff[nb + blockIdx.x], run2 = boff[2 * nb + blockIdx.x];
+  const int64_t keep_total = total[1];
+  const uint32_t below = (1u << lane) - 1u;
+  for (int rr = 0; rr < kScanRounds; ++rr) {
+    int k;
+    const ListSel q = list_sel(t, open, m, flag, Lm, start + (int64_t)rr * kScanBlock + threadIdx.x, k);
+    const uint32_t b0 = __ballot_sync(0xffffffffu, q.f);
+    const uint32_t b1 = __ballot_sync(0xffffffffu, q.keep);
+    const uint32_t b2 = __ballot_sync(0xffffffffu, q.co);
+    if (lane == 0) {
+      wsum[0][warp] = __popc(b0);
+      wsum[1][warp] = __popc(b1);
+      wsum[2][warp] = __popc(b2);
+    }
+    __syncthreads();
+    int32_t p0 = 0, p1 = 0, p2 = 0, t0 = 0, t1 = 0, t2 = 0;
+#pragma unroll
+    for (int w = 0; w < kScanBlock / 32; ++w) {
+      const int32_t v0 = wsum[0][w], v1 = wsum[1][w], v2 = wsum[2][w];
+      p0 += w < warp ? v0 : 0;
+      p1 += w < warp ? v1 : 0;
+      p2 += w < warp ? v2 : 0;
+      t0 += v0;
+      t1 += v1;
+      t2 += v2;
+    }
+    if (q.f) {
+      const int64_t c0 = n_old + 4 * (run0 + p0 + __popc(b0 & below));
+      const int L = t.lvl[k] + 1, i = t.pi[k], j = t.pj[k];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        t.lvl[c0 + c] = (int8_t)L;
+        t.pi[c0 + c] = 2 * i + (c & 1);
+        t.pj[c0 + c] = 2 * j + (c >> 1);
+        t.child[c0 + c] = -1;
+        flag[c0 + c] = 0u;
+      }
+      t.child[k] = (int32_t)c0;
+      flag[k] = 0u;
+      if (q.co) {
+        const int64_t r2 = keep_total + 4 * (run2 + p2 + __popc(b2 & below));
+#pragma unroll
+        for (int c = 0; c < 4; ++c) next[r2 + c] = (int32_t)(c0 + c);
+      }
+    } else if (q.keep) {
+      next[run1 + p1 + __popc(b1 & below)] = k;
+    }
+    run0 += t0;
+    run1 += t1;
+    run2 += t2;
+    __syncthreads();
+  }
+}
+
 // Step vi: copy the selected nodes (leaves, or all) to the output arrays.
 struct EmitOut {
   TreeView t;
@@ -284,6 +448,45 @@ cudaError_t launch_balance(const TreeView &t, int64_t n, uint32_t *flag, uint32_
 }
 
 int64_t scan_blocks(int64_t n) { return (n + kScanItems - 1) / kScanItems; }
+
+cudaError_t launch_list_init(int32_t *list, int64_t m, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  k_iota<<<nblk(m, 256), 256, 0, st>>>(list, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_list_scan(const TreeView &t, const int32_t *open, int64_t m, double xi_crit,
+                             int xi_norm, int refine_on, uint32_t *flag, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  k_xi_scan_list<<<nblk(m, 256), 256, 0, st>>>(t, open, m, xi_crit, xi_norm, refine_on, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_list_balance(const TreeView &t, const int32_t *open, int64_t m, uint32_t *flag,
+                                uint32_t *err, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  k_balance_list<<<stride_blocks(m, 128, 16), 128, 0, st>>>(t, open, m, flag, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_list_count(const TreeView &t, const int32_t *open, int64_t m,
+                              const uint32_t *flag, int32_t *bcount, int64_t *boff,
+                              int64_t *totals, cudaStream_t st) {
+  const int64_t nb = scan_blocks(m);
+  if (nb == 0) return cudaMemsetAsync(totals, 0, 3 * sizeof(int64_t), st);
+  k_count3<<<(unsigned)nb, kScanBlock, 0, st>>>(t, open, m, flag, t.Lm, bcount, nb);
+  k_scan_blocks3<<<3, 1024, 0, st>>>(bcount, nb, boff, totals);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_list_emit(const TreeView &t, const int32_t *open, int64_t m, uint32_t *flag,
+                             const int64_t *boff, const int64_t *totals, int64_t n_old,
+                             int32_t *next, cudaStream_t st) {
+  const int64_t nb = scan_blocks(m);
+  if (nb == 0) return cudaSuccess;
+  k_emit3<<<(unsigned)nb, kScanBlock, 0, st>>>(t, open, m, flag, t.Lm, boff, totals, nb, n_old, next);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_count_flags(const uint32_t *flag, int64_t n, int32_t *bcount, int64_t *boff,
                                int64_t *total, cudaStream_t st) {

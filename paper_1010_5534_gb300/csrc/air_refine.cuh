@@ -61,6 +61,21 @@ cudaError_t launch_emit_out(const TreeView &t, const OutView &o, int all, int64_
 // Exclusive scan of nb per-block counts (one block) -> boff, total.
 cudaError_t launch_scan_offsets(const int32_t *bcount, int64_t nb, int64_t *boff, int64_t *total,
                                 cudaStream_t st);
+// Open-leaf list (leaves below the top level, ascending): steps iii-iv over it.
+cudaError_t launch_list_init(int32_t *list, int64_t m, cudaStream_t st);
+cudaError_t launch_list_scan(const TreeView &t, const int32_t *open, int64_t m, double xi_crit,
+                             int xi_norm, int refine_on, uint32_t *flag, cudaStream_t st);
+cudaError_t launch_list_balance(const TreeView &t, const int32_t *open, int64_t m, uint32_t *flag,
+                                uint32_t *err, cudaStream_t st);
+// totals[0] flagged, [1] kept, [2] flagged with children below the top level;
+// bcount / boff hold 3 x scan_blocks(m) entries.
+cudaError_t launch_list_count(const TreeView &t, const int32_t *open, int64_t m,
+                              const uint32_t *flag, int32_t *bcount, int64_t *boff,
+                              int64_t *totals, cudaStream_t st);
+// Children of the flagged entries at n_old + 4 * rank; the next list into `next`.
+cudaError_t launch_list_emit(const TreeView &t, const int32_t *open, int64_t m, uint32_t *flag,
+                             const int64_t *boff, const int64_t *totals, int64_t n_old,
+                             int32_t *next, cudaStream_t st);
 int64_t flux_blocks(int64_t n);
 cudaError_t launch_flux(FluxArgs a, double *flux, double *steps, cudaStream_t st);
 
