@@ -544,9 +544,15 @@ def main():
     load_s = time.perf_counter() - t0
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def render(mem="device", cap=None):
+    # the image a caller reads back: each leaf's level and position, column
+    # density and band intensities, and the band flux (is_leaf is all ones for
+    # a leaves-only image, and the band sum equals the intensity for one band)
+    E2E_FIELDS = ("level", "i", "j", "coldens", "intensity", "band_flux")
+
+    def render(mem="device", cap=None, fields=None):
+        kw = {"fields": fields} if fields else {}
         return g.render_adaptive(view, W["base_res"], W["max_level"], W["xi_crit"], mem=mem,
-                                 capacity=cap)
+                                 capacity=cap, **kw)
 
     if args.profile_case:
         for _ in range(args.warmup + 1):
@@ -607,13 +613,13 @@ def main():
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        rh = render(mem="host", cap=cap)
+        rh = render(mem="host", cap=cap, fields=E2E_FIELDS)
         e1.record(st)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
         e2e_steps += rh["n_steps"]
         n = rh["n_out"]
-        d2h = n * (4 + 4 + 4 + 1 + 4 + 4 * g.n_bands + 4) + 8 * g.n_bands
+        d2h = n * (4 + 4 + 4 + 4 + 4 * g.n_bands) + 8 * g.n_bands
     e2e_val = e2e_steps / (sum(e2e_ms) * 1e-3)
     if world > 1:
         t = torch.tensor([e2e_val], device="cuda")
@@ -683,7 +689,8 @@ def main():
                 "data": "synthetic", "config": cfg, "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 112,
                         "d2h_bytes_per_step": int(d2h),
-                        "ms_per_step": sum(e2e_ms) / args.steps},
+                        "ms_per_step": sum(e2e_ms) / args.steps,
+                        "fields": list(E2E_FIELDS)},
                 "gpu_launches": int(gpu_launches), "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:
