@@ -413,19 +413,30 @@ air_status render_learned(air_grid *g, const air_view *view, const air_params *p
   CU_TRY(cudaMemsetAsync(w.d_err, 0, sizeof(uint32_t), st));
   int64_t n = nbase, n_refined = 0, fallback = 0;
   int32_t sweeps = 0;
+  // steps iii-iv over the open-leaf list, as in the plain loop
+  const int64_t open_max = std::max<int64_t>(1, bound - ((int64_t)n0 << Lm) * ((int64_t)n0 << Lm));
+  for (int k = 0; k < 2; ++k)
+    CU_TRY(ensure((void **)&w.open[k], &w.open_b[k], sizeof(int32_t) * (size_t)open_max));
+  CU_TRY(ensure((void **)&w.bcount, &w.bcount_b, 3 * sizeof(int32_t) * scan_blocks(bound)));
+  CU_TRY(ensure((void **)&w.boff, &w.boff_b, 3 * sizeof(int64_t) * scan_blocks(bound)));
+  int cur = 0;
+  int64_t mo = Lm > 0 ? nbase : 0;
+  CU_TRY(launch_list_init(w.open[0], mo, st));
   for (;;) {
+    if (mo == 0) break;
     CU_TRY(prof_open(g, AIR_PHASE_SCAN, 1));
-    CU_TRY(launch_xi_scan(t, n, pr->xi_crit, pr->xi_norm, pr->refine_on, w.flag, st));
+    CU_TRY(launch_list_scan(t, w.open[cur], mo, pr->xi_crit, pr->xi_norm, pr->refine_on, w.flag, st));
     CU_TRY(prof_close(g));
     CU_TRY(prof_open(g, AIR_PHASE_BALANCE, 1));
-    CU_TRY(launch_balance(t, n, w.flag, w.d_err, st));
+    CU_TRY(launch_list_balance(t, w.open[cur], mo, w.flag, w.d_err, st));
     CU_TRY(prof_close(g));
     CU_TRY(prof_open(g, AIR_PHASE_REFINE, 2));
-    CU_TRY(launch_count_flags(w.flag, n, w.bcount, w.boff, w.d_total, st));
+    CU_TRY(launch_list_count(t, w.open[cur], mo, w.flag, w.bcount, w.boff, w.d_total, st));
     CU_TRY(prof_close(g));
-    CU_TRY(cudaMemcpyAsync(w.h_total, w.d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CU_TRY(cudaMemcpyAsync(w.h_total, w.d_total, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CU_TRY(cudaStreamSynchronize(st));
-    const int64_t nflag = *w.h_total;
+    const int64_t nflag = w.h_total[0];
+    const int64_t mo_next = w.h_total[1] + 4 * w.h_total[2];
     if (nflag == 0) break;
     const int64_t n_new = n + 4 * nflag;
     if (n_new > bound) return set_error(AIR_ERR_NUMERIC, "quadtree exceeds its bound");
@@ -434,7 +445,7 @@ air_status render_learned(air_grid *g, const air_view *view, const air_params *p
       t = w.tree(n0, Lm);
     }
     CU_TRY(prof_open(g, AIR_PHASE_REFINE, 1));
-    CU_TRY(launch_emit_children(t, w.flag, n, w.boff, n, st));
+    CU_TRY(launch_list_emit(t, w.open[cur], mo, w.flag, w.boff, w.d_total, n, w.open[cur ^ 1], st));
     CU_TRY(prof_close(g));
     // values of the new pixels: gathered from the proposal, or traced
     const int64_t m = 4 * nflag;
@@ -466,6 +477,8 @@ air_status render_learned(air_grid *g, const air_view *view, const air_params *p
     n = n_new;
     n_refined += nflag;
     ++sweeps;
+    mo = mo_next;
+    cur ^= 1;
   }
   CU_TRY(cudaMemcpyAsync(w.h_err, w.d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   CU_TRY(cudaStreamSynchronize(st));
