@@ -498,6 +498,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-proposal comparison in the default workload")
     ap.add_argument("--workload", default="air", choices=["air", "batch", "learned", "ring", "large"],
                     help="air: the benchmark line (one adaptive image of the cone grid); "
                          "batch: 64 views x 16 bands in one persistent launch vs one by one; "
@@ -534,7 +536,9 @@ def main():
 
     W = WORKLOAD
     t0 = time.perf_counter()
-    sc = scenes.cone_shock_amr(W["seed"], n_base=W["n_base"], brick=W["brick"], levels=W["levels"])
+    sc = scenes.cone_shock_amr(W["seed"], n_base=W["n_base"], brick=W["brick"], levels=W["levels"],
+                               keep_smooth=not args.no_learned)
+    sc_smooth = sc
     gen_s = time.perf_counter() - t0
     view = scenes.axis_view("+z")
     torch.cuda.synchronize()
@@ -642,6 +646,49 @@ def main():
     fix_flux = float(f["band_flux"][0])
     flux_err = abs(air_flux - fix_flux) / abs(fix_flux)
 
+    # ---- the learned depth proposal on the same image: a network trained on
+    # plain trees of other clumping seeds (outside the timed region), then
+    # the same adaptive image with the proposal, timed like the plain one
+    learned = None
+    if not args.no_learned:
+        from oracle import mlp as omlp
+        t0 = time.perf_counter()
+        xs, ys = [], []
+        for sd in range(5):
+            gs = air.Grid(scenes.reseed(sc_smooth, 100 + sd))
+            for vv in scenes.random_views(5000 + sd, 19) + [view]:
+                x, y = gs.learn_samples(vv, W["base_res"], W["max_level"], W["xi_crit"])
+                xs.append(x)
+                ys.append(y)
+            gs.close()
+        net = air.MLP(omlp.init(0, scale=1.0))
+        net.train(torch.cat(xs), torch.cat(ys), batch=8192, epochs=4, lr=1e-3)
+        del xs, ys
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        for _ in range(args.warmup):
+            g.render_learned(view, W["base_res"], W["max_level"], W["xi_crit"], net, quantile=0.8,
+                             capacity=cap)
+        lms, waves = [], 0
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            rl, stl = g.render_learned(view, W["base_res"], W["max_level"], W["xi_crit"], net,
+                                       quantile=0.8, capacity=cap)
+            e1.record(st)
+            e1.synchronize()
+            lms.append(e0.elapsed_time(e1))
+            waves = stl["waves"]
+        rp = render(cap=cap)
+        same = all(bool((rp[k] == rl[k]).all()) for k in ("level", "i", "j", "coldens", "intensity"))
+        learned = dict(ms_per_image=sum(lms) / len(lms), waves=int(waves),
+                       plain_waves=int(rp["n_sweeps"]) + 1, identical_to_plain=same,
+                       speedup_vs_plain=(tot_ms / args.steps) / (sum(lms) / len(lms)),
+                       speedup_vs_fixed=min(fixed_ms) / (sum(lms) / len(lms)),
+                       training="100 plain trees (5 other clumping seeds x 20 views), "
+                                "4 epochs", training_s=train_s)
+
     # ---- roofline of the dominant kernel (the march)
     march_ms, march_launches = prof["march"]
     per_step_steps = n_steps / args.steps
@@ -678,6 +725,7 @@ def main():
             air_speedup_vs_fixed=min(fixed_ms) / (tot_ms / args.steps),
             pixel_saving_vs_fixed=W["fixed_res"] ** 2 / (n_rays / args.steps),
             flux_rel_err_vs_fixed=flux_err,
+            learned_proposal=learned,
             phase_ms_per_image={k: v[0] / args.steps for k, v in prof.items()},
             grid_cells=int(sc.n_cells), grid_bricks=int(len(sc.brick_level)),
             grid_upload_s=load_s, scene_gen_s=gen_s,

@@ -111,11 +111,16 @@ __global__ void k_features(const float *p, const float *N, const float *tau0, co
   for (int q = 0; q < kFeat; ++q) x[(int64_t)k * kFeat + q] = f2bf(f[q]);
 }
 
-// Depth label of every base pixel: the deepest node below it (nodes [0, n)).
+// Depth label of every base pixel: the deepest node below it (nodes [0, n));
+// the labels must be zeroed first.
 __global__ void k_depth_labels(const int8_t *lvl, const int32_t *pi, const int32_t *pj, int64_t n,
                                int n0, int32_t *label) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
+  // labels start at zero (the base level); children come in groups of four
+  // at n0^2 + 4 m, all of one level: the first of each group stands for it
+  const int64_t nbase = (int64_t)n0 * n0;
+  if (k < nbase || ((k - nbase) & 3) != 0) return;
   const int L = lvl[k];
   const int b = (pj[k] >> L) * n0 + (pi[k] >> L);
   atomicMax(label + b, L);
@@ -169,10 +174,9 @@ __global__ void __launch_bounds__(256) k_prop_count(const int8_t *depth, int64_t
 }
 
 // Offsets of every base pixel's subtree (sequential within the block by a
-// shared-memory scan) and the proposal rays themselves.
-__global__ void __launch_bounds__(256) k_prop_emit(const int8_t *depth, int64_t nb, int n0,
-                                                   const int64_t *boff, int64_t *off, int8_t *plvl,
-                                                   int32_t *ppi, int32_t *ppj) {
+// shared-memory scan).
+__global__ void __launch_bounds__(256) k_prop_offsets(const int8_t *depth, int64_t nb,
+                                                      const int64_t *boff, int64_t *off) {
   __shared__ int64_t part[256];
   const int64_t s0 = (int64_t)blockIdx.x * kScanItems, s1 = min(nb, s0 + kScanItems);
   const int64_t per = (kScanItems + 255) / 256;
@@ -190,18 +194,30 @@ __global__ void __launch_bounds__(256) k_prop_emit(const int8_t *depth, int64_t 
   int64_t run = boff[blockIdx.x] + part[threadIdx.x] - c;
   for (int64_t k = a; k < b; ++k) {
     off[k] = run;
-    const int d = depth[k];
-    const int bi = (int)(k % n0), bj = (int)(k / n0);
-    for (int L = 1; L <= d; ++L) {
-      const int w = 1 << L;
-      const int64_t base = run + level_offset(L);
-      for (int q = 0; q < w * w; ++q) {
-        plvl[base + q] = (int8_t)L;
-        ppi[base + q] = (bi << L) + (q % w);
-        ppj[base + q] = (bj << L) + (q / w);
-      }
-    }
-    run += subtree(d);
+    run += subtree(depth[k]);
+  }
+}
+
+// The proposal rays: one warp per base pixel, its lanes striding over the
+// pixel's subtree (level by level, row-major within a level), so the writes
+// are coalesced and no thread carries a whole subtree.
+__global__ void __launch_bounds__(256) k_prop_fill(const int8_t *depth, int64_t nb, int n0,
+                                                   const int64_t *off, int8_t *plvl, int32_t *ppi,
+                                                   int32_t *ppj) {
+  const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k >= nb) return;
+  const int d = depth[k];
+  const int64_t base = off[k], size = subtree(d);
+  const int bi = (int)(k % n0), bj = (int)(k / n0);
+  for (int64_t r = lane; r < size; r += 32) {
+    int L = 1;
+    while (L < d && r >= level_offset(L + 1)) ++L;
+    const int64_t q = r - level_offset(L);
+    const int w = 1 << L;
+    plvl[base + r] = (int8_t)L;
+    ppi[base + r] = (bi << L) + (int)(q % w);
+    ppj[base + r] = (bj << L) + (int)(q / w);
   }
 }
 
@@ -376,7 +392,7 @@ air_status render_learned(air_grid *g, const air_view *view, const air_params *p
   CU_TRY(prof_open(g, AIR_PHASE_LEARN, 1));
   if ((s = mlp_forward(mlp, lw.x, nbase, lw.logits, st))) return s;
   CU_TRY(prof_close(g));
-  CU_TRY(prof_open(g, AIR_PHASE_LEARN, 4));
+  CU_TRY(prof_open(g, AIR_PHASE_LEARN, 5));
   k_decide<<<nblk(nbase, 256), 256, 0, st>>>(lw.logits, (int)nbase, Lm, (float)q, lw.depth);
   CU_TRY(cudaGetLastError());
   const int64_t nbb = scan_blocks(nbase);
@@ -393,7 +409,8 @@ air_status render_learned(air_grid *g, const air_view *view, const air_params *p
   CU_TRY(ensure((void **)&lw.pI, &lw.pI_b, sizeof(float) * std::max<int64_t>(P, 1) * nb));
   CU_TRY(ensure((void **)&lw.pp, &lw.pp_b, sizeof(float) * std::max<int64_t>(P, 1)));
   CU_TRY(ensure((void **)&lw.psteps, &lw.psteps_b, sizeof(uint32_t) * std::max<int64_t>(P, 1)));
-  k_prop_emit<<<(unsigned)nbb, 256, 0, st>>>(lw.depth, nbase, n0, w.boff, lw.off, lw.plvl, lw.ppi, lw.ppj);
+  k_prop_offsets<<<(unsigned)nbb, 256, 0, st>>>(lw.depth, nbase, w.boff, lw.off);
+  k_prop_fill<<<nblk(nbase * 32, 256), 256, 0, st>>>(lw.depth, nbase, n0, lw.off, lw.plvl, lw.ppi, lw.ppj);
   CU_TRY(cudaGetLastError());
   CU_TRY(prof_close(g));
   const MarchTune tune = march_tune(g, pr->fp64_level);

@@ -207,8 +207,11 @@ __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], c
     float rh;
     uint32_t xv;
     load_cell<FMT>(cells, idx, rh, xv);
+    // the compiled one-axis kernels (DIR >= 1) run 14 blocks per SM and are
+    // issue-bound: there the prefetch instructions cost more than they hide
+    constexpr int kAhead = DIR >= 1 ? 1 : kPrefetchAhead;
 #pragma unroll
-    for (int n = 2; n <= kPrefetchAhead; ++n) {
+    for (int n = 2; n <= kAhead; ++n) {
       const Idx pi = idx + (Idx)n * d1;
       prefetch_cell<FMT>(cells, pi < 0 ? (Idx)0 : (pi > plast ? plast : pi));
     }
@@ -224,8 +227,8 @@ __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], c
       float rh_n;
       uint32_t xv_n;
       load_cell<FMT>(cells, idx, rh_n, xv_n);
-      if (kPrefetchAhead > 1) {
-        const Idx pi = idx + (Idx)kPrefetchAhead * d1;
+      if (kAhead > 1) {
+        const Idx pi = idx + (Idx)kAhead * d1;
         prefetch_cell<FMT>(cells, pi < 0 ? (Idx)0 : (pi > plast ? plast : pi));
       }
       rt_cell<NBT, FMT>(r, rh, xv, ds, bc, br);
