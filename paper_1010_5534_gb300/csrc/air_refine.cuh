@@ -5,7 +5,7 @@
 namespace air {
 
 constexpr int kScanBlock = 256;
-constexpr int kScanRounds = 4;
+constexpr int kScanRounds = 2;
 constexpr int kScanItems = kScanBlock * kScanRounds;
 constexpr int kBalanceStack = 8 * kMaxLevels;
 
