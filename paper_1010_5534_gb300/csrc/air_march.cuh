@@ -110,7 +110,6 @@ __device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t aux
   } else if (FMT == kCellLam) {
     lam1 = __uint_as_float(aux);
   }
-  const float rho2ds = rho * rds;
 #pragma unroll
   for (int b = 0; b < NBT; ++b) {
     if (NBT == 1 || b < bc.nbh) {
@@ -121,8 +120,9 @@ __device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t aux
       }
       const float dtau = br.kap[b] * rds;
       const float Tn = ex2_approx(br.nk[b] * r.N);
-      const float t_small = (rho2ds * lam) * (r.T[b] * one_minus_exp_over_x(dtau));
-      const float t_large = (rho * lam * br.ik[b]) * (r.T[b] - Tn);
+      const float rl = rho * lam;
+      const float t_small = (rl * rds) * (r.T[b] * one_minus_exp_over_x(dtau));
+      const float t_large = (rl * br.ik[b]) * (r.T[b] - Tn);
       const float term = dtau < 0.25f ? t_small : t_large;
       r.T[b] = Tn;
       kahan_add(r.I[b], r.cI[b], term);
