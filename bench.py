@@ -98,7 +98,12 @@ def sample_clocks_stop(proc, f, path, window):
     except subprocess.TimeoutExpired:
         proc.kill()
     f.close()
-    rows = _parse_clock_rows(path)
+    return clock_summary(_parse_clock_rows(path), window)
+
+
+def clock_summary(rows, window):
+    """Median SM clock, max clock and throttle reasons of the samples in
+    `window`, or of all samples when fewer than 3 fall inside it."""
     sel = [r for r in rows if window[0] <= r[0] <= window[1]]
     span = "timed region"
     if len(sel) < 3:
@@ -139,10 +144,10 @@ def march_source_hash():
     return h.hexdigest()[:16]
 
 
-def march_traffic():
+def march_traffic(path=None):
     """DRAM bytes per march launch from the committed ncu summary of this
     workload, if it was taken on the current march source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_march_amr_cone128_air256.md")
+    path = path or os.path.join(ROOT, "profiles", "k_march_amr_cone128_air256.md")
     if not os.path.exists(path):
         return None
     src, val = None, None

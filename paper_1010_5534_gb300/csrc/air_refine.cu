@@ -17,26 +17,6 @@
 namespace air {
 
 // Step iii: flag every leaf below max_level whose xi >= xi_crit.
-// One thread per node (the FP64 work of the scanned leaves spreads over the
-// whole grid).
-__global__ void k_xi_scan(TreeView t, int64_t n, double xi_crit, int xi_norm, int refine_on,
-                          uint32_t *__restrict__ flag) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  flag[k] = xi_flag(t, 0, k, xi_crit, xi_norm, refine_on);
-}
-
-// Step iii, balance closure from every flagged leaf (the closure is a unique
-// fixed point, whatever order the threads reach it in). Grid-stride over the
-// nodes with a few blocks per SM: few nodes are flagged, so one thread per
-// node would spend the launch scheduling blocks that do nothing.
-__global__ void k_balance(TreeView t, int64_t n, uint32_t *__restrict__ flag,
-                          uint32_t *__restrict__ err) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k0 < n; k0 += stride)
-    if (flag[k0] != 0) balance_from(t, 0, (int)k0, flag, err);
-}
-
 // ---- warp-ballot prefix sums ------------------------------------------------
 // A block covers kScanItems = kScanRounds * kScanBlock consecutive items;
 // round r holds items [r * kScanBlock, (r + 1) * kScanBlock) of the block, one
@@ -120,31 +100,6 @@ __device__ __forceinline__ void block_scan_emit(Pred pred, Emit &emit, int64_t n
     run += tot;
     __syncthreads();
   }
-}
-
-// Step iv: four children per flagged leaf at n_old + 4 * rank.
-struct EmitChildren {
-  TreeView t;
-  int64_t n_old;
-  __device__ void operator()(int64_t k, int64_t rank) {
-    const int64_t c0 = n_old + 4 * rank;
-    const int L = t.lvl[k] + 1, i = t.pi[k], j = t.pj[k];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      t.lvl[c0 + c] = (int8_t)L;
-      t.pi[c0 + c] = 2 * i + (c & 1);
-      t.pj[c0 + c] = 2 * j + (c >> 1);
-      t.child[c0 + c] = -1;
-    }
-    t.child[k] = (int32_t)c0;
-  }
-};
-
-__global__ void __launch_bounds__(kScanBlock) k_emit_children(TreeView t, const uint32_t *flag,
-                                                              int64_t n, const int64_t *boff,
-                                                              int64_t n_old) {
-  EmitChildren e{t, n_old};
-  block_scan_emit(PredFlag{flag}, e, n, boff[blockIdx.x]);
 }
 
 // ---- open-leaf list -----------------------------------------------------------
@@ -433,20 +388,6 @@ static unsigned stride_blocks(int64_t n, int block, int per_sm) {
   return (unsigned)(need < cap ? need : cap);
 }
 
-cudaError_t launch_xi_scan(const TreeView &t, int64_t n, double xi_crit, int xi_norm,
-                           int refine_on, uint32_t *flag, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  k_xi_scan<<<nblk(n, 256), 256, 0, st>>>(t, n, xi_crit, xi_norm, refine_on, flag);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_balance(const TreeView &t, int64_t n, uint32_t *flag, uint32_t *err,
-                           cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  k_balance<<<stride_blocks(n, 128, 16), 128, 0, st>>>(t, n, flag, err);
-  return cudaGetLastError();
-}
-
 int64_t scan_blocks(int64_t n) { return (n + kScanItems - 1) / kScanItems; }
 
 cudaError_t launch_list_init(int32_t *list, int64_t m, cudaStream_t st) {
@@ -504,13 +445,6 @@ cudaError_t launch_scan_offsets(const int32_t *bcount, int64_t nb, int64_t *boff
   return cudaGetLastError();
 }
 
-cudaError_t launch_emit_children(const TreeView &t, const uint32_t *flag, int64_t n,
-                                 const int64_t *boff, int64_t n_old, cudaStream_t st) {
-  const int64_t nb = scan_blocks(n);
-  if (nb == 0) return cudaSuccess;
-  k_emit_children<<<(unsigned)nb, kScanBlock, 0, st>>>(t, flag, n, boff, n_old);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_count_leaves(const TreeView &t, int all, int64_t n, int32_t *bcount,
                                 int64_t *boff, int64_t *total, cudaStream_t st) {

@@ -45,15 +45,9 @@ struct FluxArgs {
 };
 
 cudaError_t launch_init_base(const TreeView &t, cudaStream_t st);
-cudaError_t launch_xi_scan(const TreeView &t, int64_t n, double xi_crit, int xi_norm,
-                           int refine_on, uint32_t *flag, cudaStream_t st);
-cudaError_t launch_balance(const TreeView &t, int64_t n, uint32_t *flag, uint32_t *err,
-                           cudaStream_t st);
 int64_t scan_blocks(int64_t n);
 cudaError_t launch_count_flags(const uint32_t *flag, int64_t n, int32_t *bcount, int64_t *boff,
                                int64_t *total, cudaStream_t st);
-cudaError_t launch_emit_children(const TreeView &t, const uint32_t *flag, int64_t n,
-                                 const int64_t *boff, int64_t n_old, cudaStream_t st);
 cudaError_t launch_count_leaves(const TreeView &t, int all, int64_t n, int32_t *bcount,
                                 int64_t *boff, int64_t *total, cudaStream_t st);
 cudaError_t launch_emit_out(const TreeView &t, const OutView &o, int all, int64_t n,
