@@ -107,6 +107,9 @@ namespace air {
 
 struct DeviceGrid;  // owned by the handle (defined in air_grid.cu)
 
+// Streaming multiprocessors of the current device (read once; 1 if the query fails).
+int sm_count();
+
 cudaError_t launch_march(const GridView &g, const Camera &cam, const RaySource &src,
                          const RayOut &out, const MarchTune &tune, cudaStream_t st);
 cudaError_t launch_band_sum(const float *I, int n_bands, int64_t stride, int64_t first,

@@ -3,12 +3,17 @@
 
 namespace air {
 
-// Resident blocks per SM for the one-band kernel of rays parallel to an axis.
+// Resident blocks per SM for the one-band kernels of rays parallel to an
+// axis: the throughput form (DIR 1..3, for launches of several waves) and the
+// latency form (DIR 4..6, for launches of at most kLatWaves waves of it).
 constexpr int kAxisBlocks = 14;
+constexpr int kLatBlocks = 8;
+constexpr int kLatWaves = 1;
 
 template <int NBT, int DIR>
 struct MinBlocks {
-  static constexpr int value = DIR >= 1 ? kAxisBlocks
+  static constexpr int value = DIR >= 4   ? kLatBlocks
+                               : DIR >= 1 ? kAxisBlocks
                                : (NBT <= 1 ? 8 : (NBT <= 2 ? 5 : (NBT <= 4 ? 4 : (NBT <= 8 ? 3 : 2))));
 };
 
@@ -110,13 +115,19 @@ static cudaError_t launch_t(const GridView &g, const Camera &cam, const RaySourc
   const int fp = tune.fp64_level;
 #define AIR_MARCH(N, A, F, D) k_march<N, A, F, D><<<grid, block, smem, st>>>(g, rg, src, out, fp)
   if (NBT == 1 && moving == 1) {
-    // every ray parallel to grid axis A: DIR = 1 + A
+    // every ray parallel to grid axis A: DIR = 1 + A, or 4 + A (the latency
+    // form) for a launch that fills the GPU at most kLatWaves times
     const int A = rg.Dhi[0] != 0.f ? 0 : (rg.Dhi[1] != 0.f ? 1 : 2);
+    const bool lat = blocks <= (int64_t)kLatWaves * kLatBlocks * sm_count();
 #define AIR_AXIS(D)                                                                              \
   if (g.cell_fmt == kCellRho) { if (amr) AIR_MARCH(1, true, kCellRho, D); else AIR_MARCH(1, false, kCellRho, D); } \
   else if (g.cell_fmt == kCellXq) { if (amr) AIR_MARCH(1, true, kCellXq, D); else AIR_MARCH(1, false, kCellXq, D); } \
   else { if (amr) AIR_MARCH(1, true, kCellLam, D); else AIR_MARCH(1, false, kCellLam, D); }
-    if (A == 0) { AIR_AXIS(1) }
+    if (lat) {
+      if (A == 0) { AIR_AXIS(4) }
+      else if (A == 1) { AIR_AXIS(5) }
+      else { AIR_AXIS(6) }
+    } else if (A == 0) { AIR_AXIS(1) }
     else if (A == 1) { AIR_AXIS(2) }
     else { AIR_AXIS(3) }
 #undef AIR_AXIS

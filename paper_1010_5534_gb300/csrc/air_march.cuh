@@ -178,7 +178,12 @@ __device__ __forceinline__ void prefetch_cell(const void *__restrict__ cells, Id
 // one counter, one bound); the per-launch direction makes this choice the
 // same for every thread.
 // DIR = 1 + A: the launch's rays are all parallel to grid axis A, so only the
-// one-axis form is compiled (fewer registers, more resident warps); DIR = 0
+// one-axis form is compiled (fewer registers, more resident warps), without
+// prefetch (the throughput form, for launches of several waves, which are
+// issue-bound); DIR = 4 + A: the same with the prefetch (the latency form,
+// for launches of one wave or less, where every step waits on its cell's
+// load and the prefetch shortens that wait; same arithmetic, so the same
+// results bit for bit); DIR = 0
 // chooses between the two forms at run time. (A 3-axis-only form was tried
 // for oblique launches: within 1% of DIR = 0 at 56 registers, and at 64 its
 // code ran twice as slow, so it is not kept.)
@@ -207,9 +212,9 @@ __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], c
     float rh;
     uint32_t xv;
     load_cell<FMT>(cells, idx, rh, xv);
-    // the compiled one-axis kernels (DIR >= 1) run 14 blocks per SM and are
+    // the throughput form (DIR 1..3) runs 14 blocks per SM and is
     // issue-bound: there the prefetch instructions cost more than they hide
-    constexpr int kAhead = DIR >= 1 ? 1 : kPrefetchAhead;
+    constexpr int kAhead = (DIR >= 1 && DIR <= 3) ? 1 : kPrefetchAhead;
 #pragma unroll
     for (int n = 2; n <= kAhead; ++n) {
       const Idx pi = idx + (Idx)n * d1;
@@ -573,12 +578,13 @@ __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
 // compile time): the same brick walk with the same expressions, so the same
 // bits, but only axis A's FP64 position and exit parameter are carried; the
 // other two axes keep their double-float origin (their offsets never change
-// along the ray) and every brick is entered through an A face.
-template <int NBT, int FMT, int A>
+// along the ray) and every brick is entered through an A face. DIR = 1 + A
+// (throughput form) or 4 + A (latency form).
+template <int NBT, int FMT, int DIR>
 __device__ void march_amr_axis(RTState<NBT> &r, const GridView &g, const double O[3],
                                const RayGeom &rg, double t0, int fp64_level, const BandCtx &bc,
                                const BandRegs<NBT> &br) {
-  constexpr int A1 = (A + 1) % 3, A2 = (A + 2) % 3;
+  constexpr int A = (DIR - 1) % 3, A1 = (A + 1) % 3, A2 = (A + 2) % 3;
   const int B = g.B, lb = g.log2B, Lm = g.Lm;
   const double OA = O[A];
   const bool pos = rg.Dhi[A] > 0.f;
@@ -636,7 +642,7 @@ __device__ void march_amr_axis(RTState<NBT> &r, const GridView &g, const double 
     const int64_t boff = (int64_t)code << (3 * lb);
     const void *cb = FMT == kCellRho ? (const void *)((const float *)g.cells + boff)
                                      : (const void *)((const uint2 *)g.cells + boff);
-    march_block<NBT, FMT, int, 1 + A>(r, Q, Dl, inv, tend, lc[0], lc[1], lc[2], B, B, B, B, B * B,
+    march_block<NBT, FMT, int, DIR>(r, Q, Dl, inv, tend, lc[0], lc[1], lc[2], B, B, B, B, B * B,
                                       cb, bc, br);
     if (out) break;
     if (deep) t = f2_from(te);
@@ -659,7 +665,7 @@ __device__ __forceinline__ void trace_ray(RTState<NBT> &st, const GridView &g, c
   if (ray_setup(g, rg, L, i, j, O, t0, eax)) {
     if (AMR) {
       if constexpr (DIR >= 1)
-        march_amr_axis<NBT, FMT, DIR - 1>(st, g, O, rg, t0, fp64_level, bc, br);
+        march_amr_axis<NBT, FMT, DIR>(st, g, O, rg, t0, fp64_level, bc, br);
       else
         march_amr<NBT, FMT, DIR>(st, g, O, rg, t0, eax, fp64_level, bc, br);
     } else {

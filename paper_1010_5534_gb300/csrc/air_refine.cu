@@ -373,17 +373,23 @@ cudaError_t launch_init_base(const TreeView &t, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Blocks for a grid-stride launch: enough for `per_sm` blocks on every SM.
-static unsigned stride_blocks(int64_t n, int block, int per_sm) {
+int sm_count() {
   static int sms = 0;
   if (sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
       cudaGetLastError();
-      sms = 1;
+      n = 1;
     }
+    sms = n;
   }
-  const int64_t cap = (int64_t)sms * per_sm;
+  return sms;
+}
+
+// Blocks for a grid-stride launch: enough for `per_sm` blocks on every SM.
+static unsigned stride_blocks(int64_t n, int block, int per_sm) {
+  const int64_t cap = (int64_t)sm_count() * per_sm;
   const int64_t need = (n + block - 1) / block;
   return (unsigned)(need < cap ? need : cap);
 }
