@@ -575,81 +575,56 @@ __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
 }
 
 // march_amr for a launch whose rays all run parallel to grid axis A (known at
-// compile time): the same brick walk with the same expressions, so the same
-// bits, but only axis A's FP64 position and exit parameter are carried; the
-// other two axes keep their double-float origin (their offsets never change
-// along the ray) and every brick is entered through an A face. DIR = 1 + A
-// (throughput form) or 4 + A (latency form).
+// compile time). Such a ray enters the grid, and every brick after, through an
+// A face, and crosses each brick whole: the exit parameter relative to the
+// entry is the brick's width over the direction, S |1/D_A| (in FP64 from the
+// exact width at levels >= fp64_level, else B |1/D_A| in FP32 in the brick's
+// cells), and the other two finest coordinates never change. Every kernel form
+// sends a ray with one moving axis here, so all give the same bits for it.
+// DIR = 1 + A (throughput form) or 4 + A (latency form).
 template <int NBT, int FMT, int DIR>
 __device__ void march_amr_axis(RTState<NBT> &r, const GridView &g, const double O[3],
                                const RayGeom &rg, double t0, int fp64_level, const BandCtx &bc,
                                const BandRegs<NBT> &br) {
   constexpr int A = (DIR - 1) % 3, A1 = (A + 1) % 3, A2 = (A + 2) % 3;
-  const int B = g.B, lb = g.log2B, Lm = g.Lm;
-  const double OA = O[A];
+  const int B = g.B, Lm = g.Lm;
   const bool pos = rg.Dhi[A] > 0.f;
-  const F2 O1 = f2_from(O[A1]), O2 = f2_from(O[A2]);
   int c[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) c[a] = clampi((int)floor(O[a] + t0 * rg.D[a]), 0, g.nf[a] - 1);
-  F2 t = f2_from(t0);
-  const int max_iter = 4 * (g.nf[0] + g.nf[1] + g.nf[2]);
+  const int max_iter = 4 * g.nf[A];
   int e = map_entry(g, c[0], c[1], c[2]);
   for (int it = 0; it < max_iter; ++it) {
     int lev;
     const int code = brick_of(g, e, c, lev);
     r.maxlev = max(r.maxlev, lev);
     const int shift = Lm - lev;
-    const int sb = lb + shift;
     const int S = B << shift;
-    const float scale = __int_as_float((127 - shift) << 23);  // 2^-shift
-    const float up = __int_as_float((127 + shift) << 23);     // 2^shift
-    int lc[3], anchor[3], bo[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      bo[a] = (c[a] >> sb) << sb;
-      lc[a] = (c[a] - bo[a]) >> shift;
-      anchor[a] = bo[a] + (lc[a] << shift);
-    }
-    float Q[3], Dl[3], inv[3];
-    Dl[A] = rg.Dhi[A] * scale;
+    const float up = __int_as_float((127 + shift) << 23);  // 2^shift
+    float Q[3] = {0.f, 0.f, 0.f}, Dl[3] = {0.f, 0.f, 0.f}, inv[3] = {0.f, 0.f, 0.f};
+    Dl[A] = rg.Dhi[A] * __int_as_float((127 - shift) << 23);
     inv[A] = rg.invDhi[A] * up;
-    Dl[A1] = Dl[A2] = 0.f;
-    inv[A1] = inv[A2] = 0.f;
-    Q[A] = (float)((pos ? c[A] : c[A] + 1) - anchor[A]) * scale;
-    Q[A1] = ((O1.hi - (float)anchor[A1]) + O1.lo) * scale;
-    Q[A2] = ((O2.hi - (float)anchor[A2]) + O2.lo) * scale;
-    const bool deep = lev >= fp64_level;
-    float tend;
-    double te = 0.0;
-    if (deep) {
-      const double td = (double)t.hi + (double)t.lo;
-      const double face = (double)(pos ? bo[A] + S : bo[A]);
-      const double ta = (face - OA) * rg.invD[A];
-      te = ta < td ? td : ta;
-      tend = (float)(te - td);
-    } else {
-      const float face = pos ? (float)(B - lc[A]) : (float)(-lc[A]);
-      tend = (face - Q[A]) * inv[A];
-      if (tend < 0.f) tend = 0.f;
-    }
-    int cn[3];
-    cn[A] = pos ? bo[A] + S : bo[A] - 1;
-    const bool out = cn[A] < 0 || cn[A] >= g.nf[A];
-    cn[A1] = clampi(anchor[A1] + (int)floorf(fmaf(tend, Dl[A1], Q[A1]) * up), bo[A1], bo[A1] + S - 1);
-    cn[A2] = clampi(anchor[A2] + (int)floorf(fmaf(tend, Dl[A2], Q[A2]) * up), bo[A2], bo[A2] + S - 1);
-    const int en = out ? 0 : map_entry(g, cn[0], cn[1], cn[2]);
-    const int64_t boff = (int64_t)code << (3 * lb);
+    Q[A] = pos ? 0.f : 1.f;  // entry face, in the entry cell's frame
+    int lc[3];
+    lc[A] = pos ? 0 : B - 1;
+    lc[A1] = (c[A1] >> shift) & (B - 1);
+    lc[A2] = (c[A2] >> shift) & (B - 1);
+    const float tend = lev >= fp64_level ? (float)((double)S * fabs(rg.invD[A]))
+                                         : (float)B * fabsf(inv[A]);
+    const int cn = pos ? c[A] + S : c[A] - S;
+    const bool out = cn < 0 || cn >= g.nf[A];
+    int nc[3];
+    nc[A] = cn;
+    nc[A1] = c[A1];
+    nc[A2] = c[A2];
+    const int en = out ? 0 : map_entry(g, nc[0], nc[1], nc[2]);
+    const int64_t boff = (int64_t)code << (3 * g.log2B);
     const void *cb = FMT == kCellRho ? (const void *)((const float *)g.cells + boff)
                                      : (const void *)((const uint2 *)g.cells + boff);
     march_block<NBT, FMT, int, DIR>(r, Q, Dl, inv, tend, lc[0], lc[1], lc[2], B, B, B, B, B * B,
-                                      cb, bc, br);
+                                    cb, bc, br);
     if (out) break;
-    if (deep) t = f2_from(te);
-    else t = f2_add_f(t, tend);
-    c[0] = cn[0];
-    c[1] = cn[1];
-    c[2] = cn[2];
+    c[A] = cn;
     e = en;
   }
 }
@@ -664,10 +639,19 @@ __device__ __forceinline__ void trace_ray(RTState<NBT> &st, const GridView &g, c
   int eax;
   if (ray_setup(g, rg, L, i, j, O, t0, eax)) {
     if (AMR) {
-      if constexpr (DIR >= 1)
+      if constexpr (DIR >= 1) {
         march_amr_axis<NBT, FMT, DIR>(st, g, O, rg, t0, fp64_level, bc, br);
-      else
-        march_amr<NBT, FMT, DIR>(st, g, O, rg, t0, eax, fp64_level, bc, br);
+      } else {
+        // a ray along one grid axis takes the brick walk of the one-axis forms
+        const bool m0 = rg.Dhi[0] != 0.f, m1 = rg.Dhi[1] != 0.f, m2 = rg.Dhi[2] != 0.f;
+        if (m0 + m1 + m2 == 1) {
+          if (m0) march_amr_axis<NBT, FMT, 1>(st, g, O, rg, t0, fp64_level, bc, br);
+          else if (m1) march_amr_axis<NBT, FMT, 2>(st, g, O, rg, t0, fp64_level, bc, br);
+          else march_amr_axis<NBT, FMT, 3>(st, g, O, rg, t0, fp64_level, bc, br);
+        } else {
+          march_amr<NBT, FMT, DIR>(st, g, O, rg, t0, eax, fp64_level, bc, br);
+        }
+      }
     } else {
       march_uniform<NBT, FMT, DIR>(st, g, O, rg, t0, bc, br);
     }
