@@ -14,7 +14,7 @@ template <int NBT, int DIR>
 struct MinBlocks {
   static constexpr int value = DIR >= 4   ? kLatBlocks
                                : DIR >= 1 ? kAxisBlocks
-                               : (NBT <= 1 ? 8 : (NBT <= 2 ? 5 : (NBT <= 4 ? 4 : (NBT <= 8 ? 3 : 2))));
+                               : (NBT <= 1 ? 6 : (NBT <= 2 ? 5 : (NBT <= 4 ? 4 : (NBT <= 8 ? 3 : 2))));
 };
 
 constexpr int kMarchBlock = 128;
