@@ -10,6 +10,7 @@
 // found by descending from the base node through the child links; this gives
 // the deepest existing node at a level <= L, which is the value a missing
 // neighbour takes in the stencil.
+#include <atomic>
 #include <cfloat>
 
 #include "air_tree.cuh"
@@ -374,17 +375,18 @@ cudaError_t launch_init_base(const TreeView &t, cudaStream_t st) {
 }
 
 int sm_count() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0, n = 0;
+  static std::atomic<int> sms{0};
+  int n = sms.load(std::memory_order_relaxed);
+  if (n == 0) {
+    int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
       cudaGetLastError();
       n = 1;
     }
-    sms = n;
+    sms.store(n, std::memory_order_relaxed);
   }
-  return sms;
+  return n;
 }
 
 // Blocks for a grid-stride launch: enough for `per_sm` blocks on every SM.
