@@ -12,9 +12,9 @@
  *     returning; inputs are copied, the caller keeps ownership of its arrays.
  *   - Buffers of an air_image are host or device memory, as its `mem` field
  *     says; they are caller-owned and caller-sized (`capacity` entries). Host
- *     arrays that are all page-locked (cudaHostAlloc, cudaHostRegister) are
- *     written by the output kernels directly; otherwise through device
- *     staging and copies. Either way they are complete when the call returns.
+ *     arrays are filled from device staging arrays by copies (page-locked
+ *     arrays, from cudaHostAlloc or cudaHostRegister, take them at the copy
+ *     engines' full rate). They are complete when the call returns.
  *   - Images are orthographic (the paper's observer is at 1 kpc from a box of
  *     1e18 cm, Section 3). Pixel (L, i, j) of an n0 x n0 base image has its
  *     centre at u = -H + (i + 1/2) 2H / (n0 2^L), v likewise with j, where the

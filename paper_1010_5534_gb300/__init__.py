@@ -352,6 +352,38 @@ class Grid:
             setattr(im, k, t.data_ptr())
         return im, out
 
+    def alloc_image(self, capacity, mem="device", fields=None):
+        """Output arrays for `capacity` nodes (a dict of tensors, page-locked for
+        mem="host"), to pass as `out=` to render_adaptive call after call."""
+        return self._alloc(capacity, mem, fields or self.ALL)[1]
+
+    def _image_of(self, out, mem):
+        """Image struct over caller-provided output tensors (see alloc_image)."""
+        import torch
+        spec = dict(level=torch.int32, i=torch.int32, j=torch.int32, is_leaf=torch.uint8,
+                    coldens=torch.float32, intensity=torch.float32, p=torch.float32,
+                    band_flux=torch.float64)
+        on_dev = mem == "device"
+        cap = None
+        im = Image()
+        im.mem = AIR_DEVICE if on_dev else AIR_HOST
+        for k, t in out.items():
+            if k not in spec or t.dtype != spec[k] or not t.is_contiguous():
+                raise ValueError(f"output {k!r}: wrong name, dtype or layout")
+            if t.is_cuda != on_dev:
+                raise ValueError(f"output {k!r} is not in {mem} memory")
+            if k == "band_flux":
+                if t.numel() < self.n_bands:
+                    raise ValueError("band_flux holds fewer than n_bands values")
+            else:
+                if k == "intensity" and (t.dim() != 2 or t.shape[0] != self.n_bands):
+                    raise ValueError("intensity must be [n_bands, capacity]")
+                n = t.shape[-1]
+                cap = n if cap is None else min(cap, n)
+            setattr(im, k, t.data_ptr())
+        im.capacity = max(int(cap or 1), 1)
+        return im
+
     @staticmethod
     def _result(im, out):
         n = im.n_out
@@ -434,11 +466,19 @@ class Grid:
 
     def render_adaptive(self, view, base_res, max_level, xi_crit, xi_norm=0, refine_on=0,
                         fp64_level=-1, include_interior=False, mem="device", fields=ALL,
-                        capacity=None):
-        """Adaptive image; leaves (or all traced nodes) in creation order."""
+                        capacity=None, out=None):
+        """Adaptive image; leaves (or all traced nodes) in creation order. With
+        `out` (from alloc_image) the image is written into those arrays; the
+        call fails if they are too small."""
         _check(lib().air_set_stream(self._h, _stream()))
         p = Params(int(base_res), int(max_level), float(xi_crit), int(xi_norm), int(refine_on),
                    int(fp64_level), 1 if include_interior else 0)
+        if out is not None:
+            im = self._image_of(out, mem)
+            _check(lib().air_render_adaptive(self._h, C.byref(_view(view)), C.byref(p),
+                                             C.byref(im)))
+            self._raster_src = (int(base_res), int(max_level))
+            return self._result(im, out)
         cap = capacity or max(self._cap_hint, 4 * base_res * base_res)
         im, out = self._alloc(cap, mem, fields)
         st = lib().air_render_adaptive(self._h, C.byref(_view(view)), C.byref(p), C.byref(im))

@@ -206,36 +206,20 @@ static void *host_locked(const void *p) {
   return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
-// Where the output kernels write: the caller's device arrays; the caller's host
-// arrays themselves when every one of them is page-locked (the kernels store
-// through the host link, no staging copy); otherwise device staging arrays that
-// finish_out copies back.
-static air_status out_view(air_grid *g, const air_image *im, int64_t n, OutView &o, bool &direct) {
+// Where the output kernels write: the caller's device arrays, or, for host
+// arrays (page-locked or not), device staging arrays that finish_out copies
+// back. The copies run on the copy engines, which move ~190 GB/s over the
+// host link of a Grace-hosted GB300 where kernel stores through the link
+// reach ~60 GB/s.
+static air_status out_view(air_grid *g, const air_image *im, int64_t n, OutView &o) {
   Workspace &w = g->ws;
   const int nb = g->gv.n_bands;
   o.n_bands = nb;
-  direct = false;
   if (im->mem == AIR_DEVICE) {
     o.level = im->level; o.i = im->i; o.j = im->j; o.is_leaf = im->is_leaf;
     o.N = im->coldens; o.p = im->p; o.I = im->intensity;
     o.stride = im->capacity;
     return AIR_OK;
-  }
-  {
-    void *q[7];
-    const void *h[7] = {im->level, im->i, im->j, im->is_leaf, im->coldens, im->p, im->intensity};
-    bool all = true;
-    for (int k = 0; k < 7; ++k) {
-      q[k] = nullptr;
-      if (h[k] && !(q[k] = host_locked(h[k]))) all = false;
-    }
-    if (all) {
-      o.level = (int32_t *)q[0]; o.i = (int32_t *)q[1]; o.j = (int32_t *)q[2];
-      o.is_leaf = (uint8_t *)q[3]; o.N = (float *)q[4]; o.p = (float *)q[5]; o.I = (float *)q[6];
-      o.stride = im->capacity;
-      direct = true;
-      return AIR_OK;
-    }
   }
   const size_t m = (size_t)std::max<int64_t>(n, 1);
   o.stride = (int64_t)m;
@@ -250,13 +234,12 @@ static air_status out_view(air_grid *g, const air_image *im, int64_t n, OutView 
   return AIR_OK;
 }
 
-// Staging -> host arrays (host-memory outputs not written directly), then band
-// flux and step count.
-static air_status finish_out(air_grid *g, air_image *im, const OutView &o, int64_t n, bool direct) {
+// Staging -> host arrays (host-memory outputs), then band flux and step count.
+static air_status finish_out(air_grid *g, air_image *im, const OutView &o, int64_t n) {
   cudaStream_t st = g->stream;
   const int nb = g->gv.n_bands;
   Workspace &w = g->ws;
-  if (im->mem == AIR_HOST && n > 0 && !direct) {
+  if (im->mem == AIR_HOST && n > 0) {
     if (im->level) CU_TRY(cudaMemcpyAsync(im->level, o.level, 4 * n, cudaMemcpyDeviceToHost, st));
     if (im->i) CU_TRY(cudaMemcpyAsync(im->i, o.i, 4 * n, cudaMemcpyDeviceToHost, st));
     if (im->j) CU_TRY(cudaMemcpyAsync(im->j, o.j, 4 * n, cudaMemcpyDeviceToHost, st));
@@ -315,14 +298,13 @@ air_status render_fixed(air_grid *g, const air_view *view, int32_t res, int32_t 
   fa.n = n; fa.child = nullptr; fa.lvl = nullptr; fa.I = w.fI; fa.stride = n; fa.steps = w.fsteps;
   fa.n_bands = nb; fa.area0 = (2.0 * cam.H / res) * (2.0 * cam.H / res); fa.partial = w.partial;
   OutView o;
-  bool direct = false;
-  if ((s = out_view(g, im, n, o, direct))) return s;
+  if ((s = out_view(g, im, n, o))) return s;
   CU_TRY(prof_open(g, AIR_PHASE_OUTPUT, 3));
   CU_TRY(launch_flux(fa, w.d_flux, w.d_flux + nb, st));
   k_fixed_out<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, res, w.fN, w.fp, w.fI, nb, o);
   CU_TRY(cudaGetLastError());
   CU_TRY(prof_close(g));
-  s = finish_out(g, im, o, n, direct);
+  s = finish_out(g, im, o, n);
   if (s) return s;
   CU_TRY(prof_resolve(g));
   return AIR_OK;
@@ -532,14 +514,13 @@ air_status output_tree(air_grid *g, const Camera &cam, const air_params *pr, air
   fa.stride = spectra_dev ? spectra_cap : t.cap;
   fa.n_bands = nb; fa.area0 = (2.0 * cam.H / n0) * (2.0 * cam.H / n0); fa.partial = w.partial;
   OutView o;
-  bool direct = false;
-  if ((s = out_view(g, im, n_out, o, direct))) return s;
+  if ((s = out_view(g, im, n_out, o))) return s;
   CU_TRY(prof_open(g, AIR_PHASE_OUTPUT, 5));
   CU_TRY(launch_flux(fa, w.d_flux, w.d_flux + nb, st));
   CU_TRY(launch_count_leaves(t, all, n, w.bcount, w.boff, w.d_total, st));
   CU_TRY(launch_emit_out(t, o, all, n, w.boff, st));
   CU_TRY(prof_close(g));
-  s = finish_out(g, im, o, n_out, direct);
+  s = finish_out(g, im, o, n_out);
   if (s) return s;
   CU_TRY(prof_resolve(g));
   return AIR_OK;

@@ -339,9 +339,34 @@ def test_cone_full_size_sampled():
     assert err < 1e-2
 
 
+def test_reused_output_arrays(cone4):
+    """render_adaptive(out=...) writes the image into caller-held arrays, call
+    after call, with the bits of a fresh call; arrays that are too small fail
+    with AIR_ERR_CAPACITY."""
+    sc, g, o = cone4
+    v = scenes.random_views(5, 1)[0]
+    ref = g.render_adaptive(v, 16, 2, 0.4)
+    n = ref["n_out"]
+    fields = ("level", "i", "j", "coldens", "intensity", "band_flux")
+    for mem in ("device", "host"):
+        buf = g.alloc_image(n + 7, mem, fields)
+        for rep in range(2):
+            r = g.render_adaptive(v, 16, 2, 0.4, mem=mem, out=buf)
+            assert r["n_out"] == n
+            for k in fields:
+                assert (np_(r[k]) == np_(ref[k])).all(), (mem, rep, k)
+            assert r["intensity"].data_ptr() == buf["intensity"].data_ptr()
+    small = g.alloc_image(max(n // 2, 1), "device", fields)
+    with pytest.raises(air.AirError) as e:
+        g.render_adaptive(v, 16, 2, 0.4, out=small)
+    assert e.value.status == air.AIR_ERR_CAPACITY
+    with pytest.raises(ValueError):
+        g.render_adaptive(v, 16, 2, 0.4, mem="host", out=small)
+
+
 def test_pageable_host_outputs_use_staging(cone4):
-    """Host outputs in pageable memory go through device staging and copies;
-    page-locked ones are written by the kernels directly. Same bits."""
+    """Host outputs in pageable memory go through device staging and copies,
+    as page-locked ones do. Same bits as device outputs."""
     import ctypes as C
     sc, g, o = cone4
     v = scenes.random_views(3, 1)[0]
