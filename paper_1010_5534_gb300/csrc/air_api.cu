@@ -195,8 +195,8 @@ __global__ void k_fixed_out(int64_t n, int res, const float *N, const float *p, 
     for (int b = 0; b < n_bands; ++b) o.I[(int64_t)b * o.stride + k] = I[(int64_t)b * n + k];
 }
 
-// Output arrays: the caller's (device memory) or staging buffers (host memory).
-// Device address of page-locked host memory (NULL if p is not page-locked).
+// Device address of page-locked host memory (NULL if p is not page-locked):
+// the streamed spectra's flux kernel reads the host array through it.
 static void *host_locked(const void *p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {

@@ -114,3 +114,32 @@ def test_struct_layouts_match_header(tmp_path):
         assert C.sizeof(cls) == int(got[cname]), cname
         for f, _ in cls._fields_:
             assert getattr(cls, f).offset == int(got[f"{cname}.{f}"]), (cname, f)
+
+
+def test_caller_output_arrays_are_checked_on_the_host():
+    """Grid._image_of (the out= path of render_adaptive) builds the Image from
+    caller-held arrays: capacity = the shortest per-node array, pointers set,
+    and wrong dtypes, shapes or memory kinds rejected before any call."""
+    import types
+
+    import torch
+    fake = types.SimpleNamespace(n_bands=2)
+    n = 11
+    out = dict(level=torch.zeros(n, dtype=torch.int32), i=torch.zeros(n + 3, dtype=torch.int32),
+               coldens=torch.zeros(n, dtype=torch.float32),
+               intensity=torch.zeros((2, n + 1), dtype=torch.float32),
+               band_flux=torch.zeros(2, dtype=torch.float64))
+    im = air.Grid._image_of(fake, out, "host")
+    assert im.mem == air.AIR_HOST and im.capacity == n
+    assert im.level == out["level"].data_ptr() and im.intensity == out["intensity"].data_ptr()
+    assert not im.j and not im.p
+    bad = [dict(out, level=torch.zeros(n, dtype=torch.int64)),
+           dict(out, intensity=torch.zeros((3, n), dtype=torch.float32)),
+           dict(out, band_flux=torch.zeros(1, dtype=torch.float64)),
+           dict(out, coldens=torch.zeros((n, 2), dtype=torch.float32)[:, 0]),
+           dict(out, bogus=torch.zeros(n))]
+    for o in bad:
+        with pytest.raises(ValueError):
+            air.Grid._image_of(fake, o, "host")
+    with pytest.raises(ValueError):
+        air.Grid._image_of(fake, out, "device")   # host tensors for device outputs
