@@ -10,10 +10,12 @@
 // coordinate plus a ray parameter t (world length). Inside a block of cells
 // (the whole uniform grid, or one AMR brick) an Amanatides-Woo DDA in FP32
 // local coordinates yields the exact chord of each cell. AMR bricks are found
-// by descending the brick octree from the level-0 brick; a brick is left
+// through a dense map over the finest cells (at the finest brick level that
+// fits 2^24 entries, with an octree descent below it); a brick is left
 // through the face with the smallest exit parameter and the next brick is the
 // one holding the finest cell across that face, so no cell is skipped or
-// visited twice. Bricks at level >= fp64_level compute their entry point and
+// visited twice. A ray along one grid axis crosses every brick whole, and its
+// walk (march_amr_axis) carries no ray parameter. Bricks at level >= fp64_level compute their entry point and
 // exit parameter in FP64. Coarser bricks compute the entry point in
 // double-float (pairs of FP32 with error-free sums and products), since FP64
 // issues at a small fraction of the FP32 rate on this GPU. Either way the
@@ -171,7 +173,8 @@ __device__ __forceinline__ void prefetch_cell(const void *__restrict__ cells, Id
 // transfer step, so the load latency overlaps that arithmetic, and the cell
 // kPrefetchAhead steps further along the axis the ray crosses fastest is
 // requested from L1 at every step (clamped into the block), so most loads
-// find their line already on the way. The loop body is straight-line code
+// find their line already on the way (every form but the one-axis throughput
+// form, below). The loop body is straight-line code
 // (the axis to step, the next index and the transfer form are selected, not
 // branched on); its one branch is the exit from the block. A ray parallel to
 // a grid axis takes a one-axis form of the same loop (one boundary parameter,
@@ -184,7 +187,7 @@ __device__ __forceinline__ void prefetch_cell(const void *__restrict__ cells, Id
 // for launches of one wave or less, where every step waits on its cell's
 // load and the prefetch shortens that wait; same arithmetic, so the same
 // results bit for bit); DIR = 0
-// chooses between the two forms at run time. (A 3-axis-only form was tried
+// chooses between the one-axis and the 3-axis loop at run time. (A 3-axis-only form was tried
 // for oblique launches: within 1% of DIR = 0 at 56 registers, and at 64 its
 // code ran twice as slow, so it is not kept.)
 template <int NBT, int FMT, typename Idx, int DIR = 0>
