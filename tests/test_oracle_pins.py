@@ -285,6 +285,57 @@ def test_optically_thin_flux_equals_grid_sum():
     assert flux == pytest.approx(grid, rel=1e-12)
 
 
+def _dense_cell_ids(scene):
+    """Finest-level dense array of cell identifiers (brick, local cell), built
+    directly from the brick list: equal ids mark one (possibly coarse) cell."""
+    nx, ny, nz = scene.finest_n
+    ids = np.full((nz, ny, nx), -1, np.int64)
+    B, Lm = scene.brick, scene.max_level
+    for b in range(len(scene.brick_level)):
+        s = 1 << (Lm - scene.brick_level[b])
+        ox, oy, oz = scene.brick_origin[b]
+        loc = b * B ** 3 + np.arange(B ** 3).reshape(B, B, B)
+        ids[oz:oz + B * s, oy:oy + B * s, ox:ox + B * s] = \
+            np.repeat(np.repeat(np.repeat(loc, s, 0), s, 1), s, 2)
+    assert (ids >= 0).all()
+    return ids
+
+
+@pytest.mark.parametrize("axis", ["+x", "-x", "+y", "-y", "+z", "-z"])
+def test_amr_axis_columns_by_definition(axis):
+    """Rays along a grid axis through a three-level brick grid, one per finest
+    column: N = sum of rho ds down the column, the step count = the number of
+    distinct cells it crosses, and (kappa = 0) I = sum of j ds, each read off
+    dense finest-level arrays. Pins the brick lookup, the column each pixel's
+    ray runs down and the merging of a coarse cell's finest pieces into one
+    chord (the order of travel is pinned by the two-slab test)."""
+    sc = scenes.cone_shock_amr(3, n_base=16, brick=4, levels=2, kappa0=0.0, thickness=0.15)
+    assert len(set(sc.brick_level.tolist())) == 3
+    rho3, T3 = _dense_fields(sc)
+    ids = _dense_cell_ids(sc)
+    lam3 = _lam_vec(sc, 0, T3.ravel()).reshape(T3.shape)
+    res = sc.finest_n[0]
+    h = [(sc.hi[a] - sc.lo[a]) / sc.finest_n[a] for a in range(3)]
+    v = scenes.axis_view(axis)
+    img = oracle.Oracle(sc).fixed(v, res)
+    multi = 0
+    for k in range(res * res):
+        org, d = _ray(v, res, 0, img["i"][k], img["j"][k])
+        a = int(np.argmax(np.abs(d)))
+        sel = [int(np.floor((org[c] - sc.lo[c]) / h[c])) for c in range(3)]
+        sel[a] = slice(None)
+        key = (sel[2], sel[1], sel[0])
+        r, cid, lam = rho3[key], ids[key], lam3[key]
+        if d[a] < 0:
+            r, cid, lam = r[::-1], cid[::-1], lam[::-1]
+        steps = 1 + int(np.count_nonzero(np.diff(cid)))
+        multi += steps < len(cid)
+        assert img["steps"][k] == steps
+        assert img["col"][k] == pytest.approx(r.sum() * h[a], rel=1e-12)
+        assert img["inten"][k, 0] == pytest.approx((r * r * lam).sum() * h[a], rel=1e-12)
+    assert multi > res  # many columns cross coarse cells
+
+
 def test_amr_single_level_equals_uniform():
     sc = scenes.random_uniform(5, n=(8, 8, 8), kappa=0.3)
     am = scenes.as_amr_single_level(sc, 4)
