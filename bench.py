@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -307,7 +308,6 @@ def run_learned(args):
     learned and plain renders are compared on held-out seeds."""
     import torch
     import paper_1010_5534_gb300 as air
-    from oracle import mlp as omlp
     air.build()
     W = WORKLOAD
     n0, Lm, xc = W["base_res"], W["max_level"], W["xi_crit"]
@@ -333,7 +333,7 @@ def run_learned(args):
     Y = torch.cat(ys)
     del xs, ys
     counts = torch.bincount(Y.long(), minlength=5).cpu().tolist()
-    net = air.MLP(omlp.init(0, scale=1.0))
+    net = air.MLP(scenes.mlp_init(0, scale=1.0))
     t = time.perf_counter()
     hist = net.train(X, Y, batch=8192, epochs=args.steps, lr=1e-3)
     torch.cuda.synchronize()
@@ -399,7 +399,6 @@ def run_large(args):
     same grid) view by view, and fixed 8192^2 images (two views timed)."""
     import torch
     import paper_1010_5534_gb300 as air
-    from oracle import mlp as omlp
     air.build()
     W = LARGE
     n0, Lm, xc = W["base_res"], W["max_level"], W["xi_crit"]
@@ -449,7 +448,7 @@ def run_large(args):
     del xs, ys
     torch.cuda.synchronize()
     data_s = time.perf_counter() - t
-    net = air.MLP(omlp.init(0, scale=1.0))
+    net = air.MLP(scenes.mlp_init(0, scale=1.0))
     t = time.perf_counter()
     net.train(X, Y, batch=8192, epochs=4, lr=1e-3)
     torch.cuda.synchronize()
@@ -511,6 +510,9 @@ def main():
                          "learned: train the depth network on 2000 plain trees, evaluate")
     ap.add_argument("--seeds", type=int, default=40)
     ap.add_argument("--views", type=int, default=50)
+    ap.add_argument("--clocks-file", default=None,
+                    help="keep the nvidia-smi clock samples here ({rank} is replaced by the rank); "
+                         "default: a temporary file")
     ap.add_argument("--profile-case", action="store_true",
                     help="one adaptive image of the workload after --warmup images, then exit "
                          "(the case profiled with ncu)")
@@ -570,8 +572,8 @@ def main():
         print(json.dumps({"profile_case": "air", "rays": r["n_rays"], "steps": r["n_steps"],
                           "sweeps": r["n_sweeps"]}), flush=True)
         return
-    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") \
-        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/air_clocks_{os.getpid()}.csv"
+    clk_path = args.clocks_file.replace("{rank}", str(rank)) if args.clocks_file else \
+        os.path.join(tempfile.gettempdir(), f"air_clocks_{os.getpid()}_rank{rank}.csv")
     proc, fh = sample_clocks_start(clk_path)
     r = render()
     cap = r["n_out"]
@@ -662,7 +664,6 @@ def main():
     # the same adaptive image with the proposal, timed like the plain one
     learned = None
     if not args.no_learned:
-        from oracle import mlp as omlp
         t0 = time.perf_counter()
         xs, ys = [], []
         for sd in range(5):
@@ -672,7 +673,7 @@ def main():
                 xs.append(x)
                 ys.append(y)
             gs.close()
-        net = air.MLP(omlp.init(0, scale=1.0))
+        net = air.MLP(scenes.mlp_init(0, scale=1.0))
         net.train(torch.cat(xs), torch.cat(ys), batch=8192, epochs=4, lr=1e-3)
         del xs, ys
         torch.cuda.synchronize()

@@ -342,16 +342,21 @@ AIR_API air_status air_render_raster(air_grid *g, int32_t quantity, int32_t band
  *   is_leaf is NULL) of intensity[b * stride + k] * area0 / 4^level[k]
  *   (level 0 if level is NULL); area0 is the pixel area at level 0, e.g.
  *   (2H / base_res)^2. The result matches the band_flux of the render that
- *   produced the arrays up to FP64 summation order.
- * All arrays are device memory (checked); the work is queued on `stream` (a
+ *   produced the arrays up to FP64 summation order. Every counted level[k]
+ *   must lie in [0, 20] (the levels a render can produce); a counted entry
+ *   outside that range makes every band_flux entry NaN.
+ * All arrays are device memory of the current device (checked; managed memory
+ * is accepted); the work is queued on `stream` (a
  * cudaStream_t, NULL = legacy default stream) and band_flux is valid once the
  * stream reaches that point; the call does not synchronise.
  * Scratch: a fixed 512 KiB device array inside this library (1024 partial sums
  * x 64 bands), which every GPU that loads the library holds until the process
- * exits. Limits: 1 <= n_bands <= 64 and 0 <= n <= 2^31 - 1; larger requests
- * fail with AIR_ERR_ARG. The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture. Every call shares the array and
+ * exits. Limits: 1 <= n_bands <= 64, 0 <= n <= 2^31 - 1, n <= stride, and
+ * (n_bands - 1) * stride + n within int64; other requests fail with
+ * AIR_ERR_ARG. The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture. The address is kept until the process
+ * exits, so do not call this across a cudaDeviceReset. Every call shares the array and
  * overwrites the partial sums it uses, so nothing needs clearing, but calls
  * whose work overlaps on the GPU (other streams, other threads) race on it. */
 AIR_API air_status air_band_flux_static(const float *intensity, int64_t stride, int32_t n_bands,

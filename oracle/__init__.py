@@ -64,6 +64,12 @@ class Replay(C.Structure):
                 ("p_int", C.c_void_p), ("p_col", C.c_void_p)]
 
 
+class Hybrid(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("margin", C.c_double), ("n_decisions", C.c_int64),
+                ("n_undecided", C.c_int64), ("n_taken_from_other", C.c_int64),
+                ("n_unresolved", C.c_int64)]
+
+
 class Tree(C.Structure):
     _fields_ = [("capacity", C.c_int64), ("n_nodes", C.c_int64), ("n_leaves", C.c_int64),
                 ("n_refined", C.c_int64), ("n_sweeps", C.c_int64), ("n_steps", C.c_int64),
@@ -88,6 +94,9 @@ def lib():
             L.orc_air.restype = C.c_int32
             L.orc_air.argtypes = [C.c_void_p, C.POINTER(ViewS), C.POINTER(Params),
                                   C.POINTER(Tree), C.POINTER(Replay)]
+            L.orc_air_hybrid.restype = C.c_int32
+            L.orc_air_hybrid.argtypes = [C.c_void_p, C.POINTER(ViewS), C.POINTER(Params),
+                                         C.POINTER(Tree), C.POINTER(Replay), C.POINTER(Hybrid)]
             L.orc_xi.restype = C.c_double
             L.orc_xi.argtypes = [C.c_void_p, C.c_int32]
             L.orc_lambda.restype = C.c_double
@@ -181,9 +190,15 @@ class Oracle:
                     inten=inten, steps=steps)
 
     def air(self, view, base_res, max_level, xi_crit, xi_norm=0, refine_on=0,
-            capacity=None, replay=None):
+            capacity=None, replay=None, other=None, rtol=1e-5, margin=2.0):
         """The AIR sweep loop. Returns every traced node (interior ones included)
-        in creation order; `leaf` marks the pixels of the final image."""
+        in creation order; `leaf` marks the pixels of the final image.
+
+        replay: take pixel values from this table (level, i, j, p_int, p_col)
+        instead of tracing. other: trace, but take every undecided flag
+        decision (|xi - xi_crit| within `margin` x the first-order change of xi
+        when each stencil value moves by `rtol` of itself) from this table's
+        values; the counts come back under "hybrid"."""
         if capacity is None:
             capacity = sum((base_res << l) ** 2 for l in range(max_level + 1))
         nb = self.n_bands
@@ -197,16 +212,26 @@ class Oracle:
         for k in ("level", "i", "j", "leaf", "parent", "col", "inten", "p_int", "steps"):
             setattr(t, k, _p(out[k]))
         p = Params(base_res, max_level, float(xi_crit), xi_norm, refine_on)
-        rp = None
         keep = []
-        if replay is not None:
-            arrs = [np.ascontiguousarray(replay[k], dtype=dt) for k, dt in
+
+        def table(src):
+            arrs = [np.ascontiguousarray(src[k], dtype=dt) for k, dt in
                     (("level", np.int32), ("i", np.int32), ("j", np.int32),
                      ("p_int", np.float64), ("p_col", np.float64))]
             keep.extend(arrs)
-            rp = Replay(len(arrs[0]), *[_p(a) for a in arrs])
-        e = lib().orc_air(self.ctx, C.byref(_view(view)), C.byref(p), C.byref(t),
-                          C.byref(rp) if rp is not None else None)
+            return Replay(len(arrs[0]), *[_p(a) for a in arrs])
+
+        hy = None
+        if other is not None:
+            if replay is not None:
+                raise ValueError("replay and other are exclusive")
+            hy = Hybrid(float(rtol), float(margin), 0, 0, 0, 0)
+            e = lib().orc_air_hybrid(self.ctx, C.byref(_view(view)), C.byref(p), C.byref(t),
+                                     C.byref(table(other)), C.byref(hy))
+        else:
+            rp = table(replay) if replay is not None else None
+            e = lib().orc_air(self.ctx, C.byref(_view(view)), C.byref(p), C.byref(t),
+                              C.byref(rp) if rp is not None else None)
         if e:
             raise OracleError(f"orc_air failed ({e})")
         n = t.n_nodes
@@ -217,6 +242,10 @@ class Oracle:
         lv = res["level"][res["leaf"] == 1]
         area = (2.0 * H / (base_res * 2.0 ** lv)) ** 2
         res["band_flux"] = (res["inten"][res["leaf"] == 1] * area[:, None]).sum(axis=0)
+        if hy is not None:
+            res["hybrid"] = dict(decisions=hy.n_decisions, undecided=hy.n_undecided,
+                                 taken_from_other=hy.n_taken_from_other,
+                                 unresolved=hy.n_unresolved)
         return res
 
     def lam(self, band, T):

@@ -365,10 +365,13 @@ static int32_t deepest(const node_maps *m, int L, int64_t i, int64_t j) {
   return -1;
 }
 
-static double node_xi(const orc_tree *t, const node_maps *m, int64_t k, int which, int xi_norm) {
+/* Stencil of node k (Eq. 2 at level L): the node whose value each of the nine
+ * positions takes, indexed [dj+1][di+1]. Positions outside the image are
+ * clamped to its edge; a position with no node at level L takes the deepest
+ * existing node at a level <= L covering it. */
+static void stencil_nodes(const orc_tree *t, const node_maps *m, int64_t k, int32_t q[9]) {
   int L = t->level[k];
   int64_t nl = (int64_t)m->n0 << L;
-  double s[9];
   for (int dj = -1; dj <= 1; ++dj)
     for (int di = -1; di <= 1; ++di) {
       int64_t ii = (int64_t)t->i[k] + di, jj = (int64_t)t->j[k] + dj;
@@ -376,15 +379,73 @@ static double node_xi(const orc_tree *t, const node_maps *m, int64_t k, int whic
       if (ii > nl - 1) ii = nl - 1;
       if (jj < 0) jj = 0;
       if (jj > nl - 1) jj = nl - 1;
-      int32_t q = deepest(m, L, ii, jj);
-      s[3 * (dj + 1) + (di + 1)] = which ? t->col[q] : t->p_int[q];
+      q[3 * (dj + 1) + (di + 1)] = deepest(m, L, ii, jj);
     }
-  return orc_xi(s, xi_norm);
 }
 
 typedef struct {
   int64_t *idx[ORC_MAX_LEVELS];
 } replay_maps;
+
+/* First-order bound of how far xi can move when each stencil value s_k moves
+ * by up to rtol |s_k| (the tolerance the GPU's pixel values are held to): the
+ * sum over the nine positions of the larger one-sided change of xi. One-sided
+ * changes (not a central difference) keep the larger slope at the kinks of
+ * the |.| terms of the denominator. */
+static double xi_margin(const double s[9], int xi_norm, double rtol) {
+  const double x0 = orc_xi(s, xi_norm);
+  double w[9], d = 0.0;
+  memcpy(w, s, sizeof(w));
+  for (int k = 0; k < 9; ++k) {
+    const double tol = rtol * fabs(s[k]);
+    if (tol == 0.0) continue;
+    w[k] = s[k] + tol;
+    const double a = fabs(orc_xi(w, xi_norm) - x0);
+    w[k] = s[k] - tol;
+    const double b = fabs(orc_xi(w, xi_norm) - x0);
+    w[k] = s[k];
+    d += a > b ? a : b;
+  }
+  return d;
+}
+
+/* One flag decision of the scan for parameter `which` (0 intensity, 1 column
+ * density) of node k. Plain mode (h NULL): xi >= xi_crit on this tree's
+ * values. Hybrid mode: the same, unless |xi - xi_crit| <= margin x the
+ * first-order bound above ("undecided": within the value tolerance either
+ * answer is correct); an undecided decision is taken from the other side's
+ * values of the same nine stencil nodes, looked up by (level, i, j), when all
+ * nine are there. */
+static int decide(const orc_tree *t, const node_maps *m, int64_t k, int which,
+                  const orc_params *p, const orc_replay *other, const replay_maps *om,
+                  orc_hybrid *h) {
+  int32_t q[9];
+  double s[9];
+  stencil_nodes(t, m, k, q);
+  for (int x = 0; x < 9; ++x) s[x] = which ? t->col[q[x]] : t->p_int[q[x]];
+  const double xi = orc_xi(s, p->xi_norm);
+  const int own = xi >= p->xi_crit;
+  if (!h) return own;
+  h->n_decisions += 1;
+  const double d = h->margin * xi_margin(s, p->xi_norm, h->rtol);
+  if (fabs(xi - p->xi_crit) > d) return own;
+  h->n_undecided += 1;
+  double so[9];
+  for (int x = 0; x < 9; ++x) {
+    const int32_t n = q[x];
+    const int L = t->level[n];
+    const int64_t nl = (int64_t)m->n0 << L;
+    const int64_t r = om->idx[L][(int64_t)t->j[n] * nl + t->i[n]];
+    if (r < 0) {
+      h->n_unresolved += 1;
+      return own;
+    }
+    so[x] = which ? other->p_col[r] : other->p_int[r];
+  }
+  const int oth = orc_xi(so, p->xi_norm) >= p->xi_crit;
+  if (oth != own) h->n_taken_from_other += 1;
+  return oth;
+}
 
 static int32_t fill_nodes(const orc_ctx *c, const orc_view *v, int n0, orc_tree *t, int64_t a,
                           int64_t b, const orc_replay *rp, const replay_maps *rm) {
@@ -413,9 +474,14 @@ static int32_t fill_nodes(const orc_ctx *c, const orc_view *v, int n0, orc_tree 
   return ORC_OK;
 }
 
-int32_t orc_air(const orc_ctx *c, const orc_view *v, const orc_params *p, orc_tree *t,
-                const orc_replay *rp) {
+/* The AIR sweep loop. rp: pixel values come from this table instead of
+ * tracing (replay). other + h: hybrid decisions (see decide); values are
+ * traced. */
+static int32_t air_loop(const orc_ctx *c, const orc_view *v, const orc_params *p, orc_tree *t,
+                        const orc_replay *rp, const orc_replay *other, orc_hybrid *h) {
   if (!c || !v || !p || !t) return ORC_ERR_ARG;
+  if ((other != NULL) != (h != NULL) || (other && rp)) return ORC_ERR_ARG;
+  const orc_replay *tab = rp ? rp : other; /* the table the maps index */
   const int n0 = p->base_res, Lm = p->max_level;
   if (n0 < 1 || Lm < 0 || Lm >= ORC_MAX_LEVELS || !(p->xi_crit >= 0.0) || p->refine_on < 0 ||
       p->refine_on > 2 || (p->xi_norm != 0 && p->xi_norm != 1))
@@ -435,21 +501,22 @@ int32_t orc_air(const orc_ctx *c, const orc_view *v, const orc_params *p, orc_tr
     m.map[l] = (int32_t *)malloc(sizeof(int32_t) * nl * nl);
     if (!m.map[l]) { err = ORC_ERR_OOM; goto done; }
     for (int64_t q = 0; q < nl * nl; ++q) m.map[l][q] = -1;
-    if (rp) {
+    if (tab) {
       rm.idx[l] = (int64_t *)malloc(sizeof(int64_t) * nl * nl);
       if (!rm.idx[l]) { err = ORC_ERR_OOM; goto done; }
       for (int64_t q = 0; q < nl * nl; ++q) rm.idx[l][q] = -1;
     }
   }
-  if (rp) {
-    for (int64_t r = 0; r < rp->n; ++r) {
-      int L = rp->level[r];
+  if (tab) {
+    for (int64_t r = 0; r < tab->n; ++r) {
+      int L = tab->level[r];
       if (L < 0 || L > Lm) continue;
       int64_t nl = (int64_t)n0 << L;
-      if (rp->i[r] < 0 || rp->i[r] >= nl || rp->j[r] < 0 || rp->j[r] >= nl) continue;
-      rm.idx[L][(int64_t)rp->j[r] * nl + rp->i[r]] = r;
+      if (tab->i[r] < 0 || tab->i[r] >= nl || tab->j[r] < 0 || tab->j[r] >= nl) continue;
+      rm.idx[L][(int64_t)tab->j[r] * nl + tab->i[r]] = r;
     }
   }
+  if (h) h->n_decisions = h->n_undecided = h->n_taken_from_other = h->n_unresolved = 0;
   /* step (i): base image, row-major */
   int64_t n = 0;
   for (int j = 0; j < n0; ++j)
@@ -469,8 +536,8 @@ int32_t orc_air(const orc_ctx *c, const orc_view *v, const orc_params *p, orc_tr
       flag[k] = 0;
       if (!t->leaf[k] || t->level[k] >= Lm) continue;
       int f = 0;
-      if (p->refine_on == 0 || p->refine_on == 2) f |= node_xi(t, &m, k, 0, p->xi_norm) >= p->xi_crit;
-      if (p->refine_on == 1 || p->refine_on == 2) f |= node_xi(t, &m, k, 1, p->xi_norm) >= p->xi_crit;
+      if (p->refine_on == 0 || p->refine_on == 2) f |= decide(t, &m, k, 0, p, other, &rm, h);
+      if (p->refine_on == 1 || p->refine_on == 2) f |= decide(t, &m, k, 1, p, other, &rm, h);
       flag[k] = (uint8_t)f;
     }
     /* step (iii): adjacent pixels may differ by at most one level after refinement */
@@ -534,4 +601,15 @@ done:
   }
   free(flag);
   return err;
+}
+
+int32_t orc_air(const orc_ctx *c, const orc_view *v, const orc_params *p, orc_tree *out,
+                const orc_replay *replay) {
+  return air_loop(c, v, p, out, replay, NULL, NULL);
+}
+
+int32_t orc_air_hybrid(const orc_ctx *c, const orc_view *v, const orc_params *p, orc_tree *out,
+                       const orc_replay *other, orc_hybrid *h) {
+  if (!other || !h || !(h->rtol >= 0.0) || !(h->margin >= 0.0)) return ORC_ERR_ARG;
+  return air_loop(c, v, p, out, NULL, other, h);
 }

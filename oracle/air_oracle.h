@@ -93,6 +93,24 @@ int32_t orc_trace(const orc_ctx *c, const orc_view *v, int32_t n0, int64_t n_ray
 int32_t orc_air(const orc_ctx *c, const orc_view *v, const orc_params *p, orc_tree *out,
                 const orc_replay *replay);
 
+/* Tree comparison where decisions sit within the value tolerance of the
+ * threshold. The sweep loop traces its own values, but a flag decision whose
+ * |xi - xi_crit| is within margin x (first-order bound of the change of xi
+ * when each stencil value moves by rtol of itself) is "undecided" and is
+ * taken from `other`'s values of the same stencil nodes (looked up by
+ * level, i, j). A tree built this way equals the other side's tree exactly
+ * when the two differ only in undecided decisions. */
+typedef struct {
+  double rtol, margin;          /* in */
+  int64_t n_decisions;          /* out: xi evaluations of the scan */
+  int64_t n_undecided;          /* out: of those, within the margin */
+  int64_t n_taken_from_other;   /* out: undecided ones where other's answer differed */
+  int64_t n_unresolved;         /* out: undecided ones with a stencil node missing in other */
+} orc_hybrid;
+
+int32_t orc_air_hybrid(const orc_ctx *c, const orc_view *v, const orc_params *p, orc_tree *out,
+                       const orc_replay *other, orc_hybrid *h);
+
 /* Eq. 2 on a 3x3 stencil s[dj+1][di+1] (pixel (i+di, j+dj)). */
 double orc_xi(const double *s9, int32_t xi_norm);
 

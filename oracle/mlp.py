@@ -94,15 +94,3 @@ def adam(theta, m, v, g, lr, t, beta1=0.9, beta2=0.999, eps=1e-8):
     mh = m / (1 - beta1 ** t)
     vh = v / (1 - beta2 ** t)
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
-
-
-def init(seed, scale=1.0):
-    """He-style random initial parameters (biases zero), as an input for both sides."""
-    rng = np.random.Generator(np.random.PCG64(seed))
-    parts = {}
-    for name, shp in SHAPES:
-        if name.startswith("W"):
-            parts[name] = rng.standard_normal(shp) * scale * np.sqrt(2.0 / shp[0])
-        else:
-            parts[name] = np.zeros(shp)
-    return pack(parts)

@@ -553,14 +553,29 @@ def band_flux_static(intensity, n, area0, level=None, is_leaf=None, out=None):
     `stride`), `level` / `is_leaf` optional CUDA tensors, `out` a float64 CUDA
     tensor of n_bands entries (allocated here if None, by the caller's torch)."""
     import torch
+    if intensity.dim() != 2 or intensity.dtype != torch.float32 or intensity.stride(1) != 1:
+        raise ValueError("intensity must be a float32 [n_bands, stride] tensor with unit column stride")
     nb = intensity.shape[0]
+    n = int(n)
+    if not 0 <= n <= intensity.shape[1]:
+        raise ValueError(f"n = {n} outside [0, {intensity.shape[1]}]")
+    dev = intensity.device
+    for name, t, dt in (("level", level, torch.int32), ("is_leaf", is_leaf, torch.uint8)):
+        if t is not None:
+            if t.dtype != dt or t.dim() != 1 or t.stride(0) != 1 or t.numel() < n:
+                raise ValueError(f"{name} must be a contiguous {dt} tensor of at least n entries")
+            if t.device != dev:
+                raise ValueError(f"{name} is on {t.device}, intensity on {dev}")
     if out is None:
-        out = torch.empty(nb, dtype=torch.float64, device=intensity.device)
-    st = lib().air_band_flux_static(
-        C.c_void_p(intensity.data_ptr()), int(intensity.stride(0)), int(nb),
-        C.c_void_p(level.data_ptr()) if level is not None else None,
-        C.c_void_p(is_leaf.data_ptr()) if is_leaf is not None else None, int(n), float(area0),
-        C.c_void_p(out.data_ptr()), _stream())
+        out = torch.empty(nb, dtype=torch.float64, device=dev)
+    elif out.dtype != torch.float64 or out.numel() < nb or not out.is_contiguous() or out.device != dev:
+        raise ValueError("out must be a contiguous float64 tensor of n_bands entries on intensity's device")
+    with torch.cuda.device(dev):
+        st = lib().air_band_flux_static(
+            C.c_void_p(intensity.data_ptr()), int(intensity.stride(0)), int(nb),
+            C.c_void_p(level.data_ptr()) if level is not None else None,
+            C.c_void_p(is_leaf.data_ptr()) if is_leaf is not None else None, n, float(area0),
+            C.c_void_p(out.data_ptr()), _stream())
     _check(st)
     return out
 

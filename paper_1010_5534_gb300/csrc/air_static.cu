@@ -19,6 +19,9 @@ namespace air {
 constexpr int kStaticFluxBlocks = 1024;                         // partial sums per band
 constexpr int64_t kStaticFluxMaxN = ((int64_t)1 << 31) - 1;     // pixels per call
 constexpr int kStaticMaxDevices = 64;
+// Pixel levels the flux accepts: an image of base n0 has levels 0..max_level
+// with n0 << max_level <= 2^20, so no render produces a level above 20.
+constexpr int kStaticMaxLevel = 20;
 
 // [block][band] partial sums: 1024 x 64 doubles = 512 KiB per device.
 static __device__ __align__(256) double g_flux_scratch[kStaticFluxBlocks * kMaxBands];
@@ -35,7 +38,12 @@ __global__ void __launch_bounds__(256) k_flux_static_partial(
     for (int64_t k = start + threadIdx.x; k < end; k += blockDim.x) {
       if (is_leaf && !is_leaf[k]) continue;
       const int L = level ? level[k] : 0;
-      s += (double)I[(int64_t)b * stride + k] * area0 * __longlong_as_double((long long)(1023 - 2 * L) << 52);
+      // 4^-L as exponent bits for 0 <= L <= kStaticMaxLevel; a level outside
+      // that range (a corrupt or stale entry) makes the band's flux NaN
+      const double scale = (L >= 0 && L <= kStaticMaxLevel)
+                               ? __longlong_as_double((long long)(1023 - 2 * L) << 52)
+                               : __longlong_as_double(0x7ff8000000000000ll);
+      s += (double)I[(int64_t)b * stride + k] * area0 * scale;
     }
     sh[threadIdx.x] = s;
     __syncthreads();
@@ -63,7 +71,10 @@ static double *g_scratch_ptr[kStaticMaxDevices];
 static bool g_scratch_ready[kStaticMaxDevices];
 
 // Device address of the scratch array on the current device, looked up once
-// per device (host code cannot use the array's name as a device pointer).
+// per device (host code cannot use the array's name as a device pointer). The
+// address is cached for the life of the process: after cudaDeviceReset (or a
+// destroyed and re-created primary context) the module may load elsewhere, so
+// this entry point must not be used across a device reset.
 static air_status static_scratch(double **out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -81,13 +92,15 @@ static air_status static_scratch(double **out) {
   return AIR_OK;
 }
 
-static bool on_device(const void *p) {
+// Device (or managed) memory of device `dev`.
+static bool on_device(const void *p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeDevice) return a.device == dev;
+  return a.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace air
@@ -103,10 +116,16 @@ extern "C" air_status air_band_flux_static(const float *intensity, int64_t strid
     return set_error(AIR_ERR_ARG, "n %lld is outside [0, %lld], the static scratch limit", (long long)n,
                      (long long)kStaticFluxMaxN);
   if (stride < n) return set_error(AIR_ERR_ARG, "stride %lld < n %lld", (long long)stride, (long long)n);
+  // the last element read, (n_bands - 1) * stride + n - 1, must fit an int64
+  if (n_bands > 1 && stride > (INT64_MAX - n) / (n_bands - 1))
+    return set_error(AIR_ERR_ARG, "stride %lld overflows the index range for %d bands", (long long)stride, n_bands);
   if (!std::isfinite(area0) || !(area0 > 0.0)) return set_error(AIR_ERR_ARG, "area0 must be finite and > 0");
-  if (!on_device(intensity) || !on_device(band_flux) || (level && !on_device(level)) ||
-      (is_leaf && !on_device(is_leaf)))
-    return set_error(AIR_ERR_ARG, "every array must be device memory");
+  int dev = -1;
+  cudaError_t de = cudaGetDevice(&dev);
+  if (de != cudaSuccess) return cuda_fail(de, "cudaGetDevice");
+  if (!on_device(intensity, dev) || !on_device(band_flux, dev) || (level && !on_device(level, dev)) ||
+      (is_leaf && !on_device(is_leaf, dev)))
+    return set_error(AIR_ERR_ARG, "every array must be device memory of the current device (%d)", dev);
   double *scratch = nullptr;
   air_status s = static_scratch(&scratch);
   if (s != AIR_OK) return s;

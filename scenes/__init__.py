@@ -660,3 +660,24 @@ def ring_amr(n_base: int = 32, brick: int = 8, levels: int = 4, beta_g_per_cm: f
 def ring_view() -> View:
     """Face-on view along +x with (u, v) = (y, z) (the paper's Fig. 1)."""
     return View(dir=(1.0, 0.0, 0.0), up=(0.0, 0.0, 1.0), half_extent=5e17 / RING_LENGTH_UNIT_CM)
+
+
+# ---------------------------------------------------------------------------
+# Initial weights of the refinement-depth network (an input to both the GPU
+# library and the FP64 network reference; no arithmetic of the method)
+MLP_SHAPES = [("W1", (16, 64)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)),
+              ("W3", (64, 5)), ("b3", (5,))]
+
+
+def mlp_init(seed: int, scale: float = 1.0) -> np.ndarray:
+    """He-style random initial parameters (weights N(0, 2 / fan_in) x scale,
+    biases zero) as one flat FP64 vector in the library's parameter order
+    W1[16][64], b1, W2[64][64], b2, W3[64][5], b3 (input index first)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for name, shp in MLP_SHAPES:
+        if name.startswith("W"):
+            parts.append((rng.standard_normal(shp) * scale * np.sqrt(2.0 / shp[0])).ravel())
+        else:
+            parts.append(np.zeros(int(np.prod(shp))))
+    return np.concatenate(parts)

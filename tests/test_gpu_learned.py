@@ -9,7 +9,6 @@ import pytest
 import oracle
 import paper_1010_5534_gb300 as air
 import scenes
-from oracle import mlp as omlp
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -38,7 +37,7 @@ def setup():
         ys.append(y)
     X = torch.cat(xs)
     Y = torch.cat(ys)
-    net = air.MLP(omlp.init(1, scale=1.0))
+    net = air.MLP(scenes.mlp_init(1, scale=1.0))
     hist = net.train(X, Y, batch=512, epochs=30, lr=3e-3)
     return s, g, net, hist
 

@@ -8,6 +8,7 @@ import pytest
 
 import paper_1010_5534_gb300 as air
 from oracle import mlp
+import scenes
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -34,7 +35,7 @@ def _b():
 
 @pytest.mark.parametrize("n", [1, 37, 128, 1000])
 def test_forward_matches_reference(n):
-    th = mlp.init(3, scale=0.8)
+    th = scenes.mlp_init(3, scale=0.8)
     th[mlp.NPARAMS - 5:] = [0.1, -0.2, 0.3, 0.0, 0.05]
     th = th.astype(np.float32).astype(np.float64)
     Xq, _ = _data(n, n)
@@ -47,7 +48,7 @@ def test_forward_matches_reference(n):
 
 @pytest.mark.parametrize("n", [128, 300, 2049])
 def test_gradient_matches_reference(n):
-    th = mlp.init(4, scale=0.8).astype(np.float32).astype(np.float64)
+    th = scenes.mlp_init(4, scale=0.8).astype(np.float32).astype(np.float64)
     Xq, y = _data(n + 1, n)
     net = air.MLP(th)
     loss, g = net.loss_grad(_bits(Xq), torch.from_numpy(y.astype(np.int32)).cuda())
@@ -63,7 +64,7 @@ def test_gradient_matches_reference(n):
 
 
 def test_adam_steps_match_reference():
-    th = mlp.init(5, scale=0.8).astype(np.float32).astype(np.float64)
+    th = scenes.mlp_init(5, scale=0.8).astype(np.float32).astype(np.float64)
     Xq, y = _data(9, 512)
     net = air.MLP(th)
     xd, yd = _bits(Xq), torch.from_numpy(y.astype(np.int32)).cuda()
@@ -83,7 +84,7 @@ def test_training_learns_a_separable_rule():
     n = 16384
     Xq = mlp.bf16_round(rng.normal(size=(n, mlp.NIN)))
     y = np.clip((Xq[:, 0] > 0).astype(int) + (Xq[:, 1] > 0.5).astype(int) + 2 * (Xq[:, 2] > 1.0), 0, 4)
-    net = air.MLP(mlp.init(6, scale=1.0))
+    net = air.MLP(scenes.mlp_init(6, scale=1.0))
     hist = net.train(_bits(Xq), torch.from_numpy(y.astype(np.int32)).cuda(), batch=1024,
                      epochs=16, lr=3e-3)
     assert hist[-1] < 0.5 * hist[0]

@@ -11,6 +11,7 @@ import pytest
 import oracle
 import paper_1010_5534_gb300 as air
 import scenes
+import test_oracle_camera as camera_pins
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -26,7 +27,10 @@ def _built():
     air.build()
 
 
-def close(gpu, orc, what, rtol=RTOL, floor=FLOOR):
+def close(gpu, orc, what, rtol=RTOL, floor=FLOOR, max_floor_frac=1e-3):
+    """Element-wise |gpu - oracle| <= rtol |oracle| + floor max|oracle|.
+    Returns how many values pass only thanks to the absolute floor (printed;
+    at most max_floor_frac of them may)."""
     g = np.asarray(gpu, dtype=np.float64)
     o = np.asarray(orc, dtype=np.float64)
     assert g.shape == o.shape, (what, g.shape, o.shape)
@@ -38,6 +42,10 @@ def close(gpu, orc, what, rtol=RTOL, floor=FLOOR):
         raise AssertionError(f"{what}: {bad.sum()} of {bad.size} off (max |oracle| {np.abs(o).max():.4g}); "
                              f"worst at {k}: gpu {g.flat[k]!r} oracle {o.flat[k]!r} "
                              f"rel {err.flat[k] / max(abs(o.flat[k]), 1e-300):.3e}")
+    n_floor = int((err > rtol * np.abs(o)).sum())
+    print(f"[close] {what}: {g.size} values, {n_floor} within tolerance only by the floor")
+    assert n_floor <= max_floor_frac * g.size + 1, (what, n_floor, g.size)
+    return n_floor
 
 
 def np_(t):
@@ -144,6 +152,22 @@ def test_face_aligned_rays_with_inexact_reciprocal_cell_size():
             assert r["n_steps"] == int(f["steps"].sum())
 
 
+@pytest.mark.parametrize("case", range(len(camera_pins.CASES)),
+                         ids=[c[0] for c in camera_pins.CASES])
+def test_camera_axes_on_gpu(case):
+    """The hand-derived camera pins (image axis and sign of each world axis,
+    the paper's face-on ring view among them) hold for the CUDA path too."""
+    name, view, cond, expect = camera_pins.CASES[case]
+    sc = scenes.uniform_from_array(camera_pins._field(cond), kappa=0.0)
+    g = air.Grid(sc)
+    r = g.render_fixed(view, camera_pins.RES)
+    img = np_(r["intensity"])[0]
+    lit = {(int(i), int(j)) for i, j, x in zip(np_(r["i"]), np_(r["j"]), img) if x > 0.0}
+    assert lit == expect, name
+    assert np.allclose(img[img > 0.0], 2.0, rtol=1e-6)
+    g.close()
+
+
 # ------------------------------------------------------------------ adaptive images
 def nodes_of(r):
     return {k: np_(r[k]) for k in ("level", "i", "j", "is_leaf", "coldens", "p")} | \
@@ -191,25 +215,46 @@ def test_air_refinement_bit_exact_on_gpu_values(cone4, refine_on, xi_norm):
         _replay_check(g, o, v, 12, 3, 0.3, refine_on=refine_on, xi_norm=xi_norm)
 
 
-def test_air_amr_matches_oracle_on_decided_nodes(cone1):
-    """Own FP64 march on the oracle side: trees agree wherever the criterion's
-    margin exceeds the value tolerance."""
-    sc, g, o = cone1
-    v = scenes.axis_view("+z")
-    r = g.render_adaptive(v, 32, 3, 0.5, include_interior=True)
-    t = o.air(v, 32, 3, 0.5)
+def _hybrid_check(g, o, v, n0, Lm, xc, capacity=None, **kw):
+    """GPU tree against the oracle's tree from its own FP64 march. Every flag
+    decision whose xi is farther from xi_crit than twice the first-order
+    change that a 1e-5 relative change of the stencil values can cause is the
+    oracle's own; the undecided rest take the GPU's values (orc_air_hybrid).
+    The GPU tree must equal that tree node for node, and every node's values
+    must match the oracle's own trace."""
+    r = g.render_adaptive(v, n0, Lm, xc, include_interior=True, **kw)
     n = nodes_of(r)
-    key_g = set(zip(n["level"].tolist(), n["i"].tolist(), n["j"].tolist()))
-    key_o = set(zip(t["level"].tolist(), t["i"].tolist(), t["j"].tolist()))
-    diff = key_g ^ key_o
-    assert len(diff) <= 0.002 * len(key_o), len(diff)
-    # values on common nodes
-    idx_o = {k: m for m, k in enumerate(zip(t["level"].tolist(), t["i"].tolist(), t["j"].tolist()))}
-    common = [(m, idx_o[k]) for m, k in enumerate(zip(n["level"].tolist(), n["i"].tolist(),
-                                                      n["j"].tolist())) if k in idx_o]
-    gi, oi = np.array(common).T
-    close(n["coldens"][gi], t["col"][oi], "N")
-    close(n["I"][0][gi], t["inten"][oi, 0], "I")
+    other = dict(level=n["level"], i=n["i"], j=n["j"], p_int=n["p"].astype(np.float64),
+                 p_col=n["coldens"].astype(np.float64))
+    kw2 = {k: kw[k] for k in ("xi_norm", "refine_on") if k in kw}
+    t = o.air(v, n0, Lm, xc, other=other, rtol=RTOL, margin=2.0, capacity=capacity, **kw2)
+    hy = t["hybrid"]
+    print(f"[tree] {n0}^2 L{Lm} xi_crit {xc}: {t['n_nodes']} nodes, {hy['decisions']} decisions, "
+          f"{hy['undecided']} undecided, {hy['taken_from_other']} of them resolved unlike the "
+          f"oracle's own values, {hy['unresolved']} unresolvable")
+    assert hy["unresolved"] == 0
+    assert t["n_nodes"] == r["n_rays"], (t["n_nodes"], r["n_rays"])
+    for k in ("level", "i", "j"):
+        assert (t[k] == n[k]).all(), k
+    assert (t["leaf"] == n["is_leaf"]).all()
+    close(n["coldens"], t["col"], "N")
+    for b in range(t["inten"].shape[1]):
+        close(n["I"][b], t["inten"][:, b], f"I[{b}]")
+    return r, t
+
+
+def test_air_amr_matches_oracle_on_decided_nodes(cone1, cone4, wind):
+    """Own FP64 march on the oracle side: the trees agree on every decided
+    node, the undecided ones are counted."""
+    sc, g, o = cone1
+    _hybrid_check(g, o, scenes.axis_view("+z"), 32, 3, 0.5)
+    _hybrid_check(g, o, scenes.random_views(7, 1)[0], 24, 3, 0.4)
+    sc, g, o = cone4
+    for v in (scenes.axis_view("-x"), scenes.random_views(11, 1)[0]):
+        _hybrid_check(g, o, v, 16, 3, 0.3, refine_on=2)
+    sc, g, o = wind
+    for xc in (0.2, 0.5, 0.8):
+        _hybrid_check(g, o, scenes.axis_view("+z"), 16, 3, xc)
 
 
 def test_air_zero_threshold_equals_fixed_finest(cone4):
@@ -317,26 +362,59 @@ def test_bad_arguments(wind):
 
 
 # ------------------------------------------------------------------ full size (bench config)
-def test_cone_full_size_sampled():
+@pytest.fixture(scope="module")
+def cone_full():
+    sc = scenes.cone_shock_amr(0)
+    return sc, air.Grid(sc), oracle.Oracle(sc)
+
+
+def test_cone_full_size_sampled(cone_full):
     """The 128^3-base, 16^3-brick, 3-level cone-shock grid at the benchmark's
     launch configuration (256^2 base image, max level 4, xi_crit 0.5): sampled
-    leaves against the oracle ray by ray, and the tree invariants."""
-    sc = scenes.cone_shock_amr(0)
-    g = air.Grid(sc)
+    leaves against the oracle ray by ray, the tree invariants, and the band
+    flux within the metric's 1e-4 of the fixed 4096^2 image."""
+    sc, g, o = cone_full
     v = scenes.axis_view("+z")
     r = g.render_adaptive(v, 256, 4, 0.5)
     nref = (r["n_rays"] - 65536) // 4
     assert r["n_rays"] == 65536 + 4 * nref and r["n_leaves"] == 65536 + 3 * nref
     lv, i, j = np_(r["level"]), np_(r["i"]), np_(r["j"])
     rng = np.random.default_rng(0)
-    pick = rng.choice(len(lv), size=1500, replace=False)
-    o = oracle.Oracle(sc)
+    pick = rng.choice(len(lv), size=4000, replace=False)
     col, inten, _ = o.trace(v, 256, lv[pick], i[pick], j[pick])
-    close(np_(r["coldens"])[pick], col, "N", floor=1e-6)
-    close(np_(r["intensity"])[0][pick], inten[:, 0], "I", floor=1e-6)
+    close(np_(r["coldens"])[pick], col, "N")
+    close(np_(r["intensity"])[0][pick], inten[:, 0], "I")
     f = g.render_fixed(v, 4096, fields=("band_flux",))
     err = abs(np_(r["band_flux"])[0] - np_(f["band_flux"])[0]) / np_(f["band_flux"])[0]
-    assert err < 1e-2
+    print(f"[flux] AIR vs fixed 4096^2: relative error {err:.3e}")
+    assert err <= 1e-4
+
+
+def test_cone_full_size_tree_replay(cone_full):
+    """The bench image's whole quadtree (7.7 M nodes, 8 sweeps, the multi-block
+    scan and emit kernels at full width): the oracle's sweep loop fed the GPU's
+    FP32 pixel values reproduces it node for node (level, i, j, order, leaf)."""
+    sc, g, o = cone_full
+    v = scenes.axis_view("+z")
+    r = g.render_adaptive(v, 256, 4, 0.5, include_interior=True,
+                          fields=("level", "i", "j", "is_leaf", "coldens", "p"))
+    n = {k: np_(r[k]) for k in ("level", "i", "j", "is_leaf", "coldens", "p")}
+    rp = dict(level=n["level"], i=n["i"], j=n["j"], p_int=n["p"].astype(np.float64),
+              p_col=n["coldens"].astype(np.float64))
+    t = o.air(v, 256, 4, 0.5, replay=rp, capacity=int(r["n_rays"]))
+    assert t["n_nodes"] == r["n_rays"] and t["n_sweeps"] == r["n_sweeps"]
+    for k in ("level", "i", "j"):
+        assert (t[k] == n[k]).all(), k
+    assert (t["leaf"] == n["is_leaf"]).all()
+
+
+def test_cone_full_size_own_march_tree(cone_full):
+    """The same image against the oracle's own FP64 march of all 7.7 M rays:
+    identical tree on every decided node (undecided ones counted), and every
+    pixel value within tolerance."""
+    sc, g, o = cone_full
+    r, t = _hybrid_check(g, o, scenes.axis_view("+z"), 256, 4, 0.5, capacity=8_200_000)
+    assert r["n_steps"] == t["n_steps"]
 
 
 def test_reused_output_arrays(cone4):

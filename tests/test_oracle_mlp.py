@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 from oracle import mlp
+import scenes
 
 
 def _data(seed, n=40):
@@ -21,7 +22,7 @@ def _data(seed, n=40):
 @pytest.mark.parametrize("seed", [0, 1])
 def test_gradient_matches_finite_differences(seed):
     X, y = _data(seed)
-    th = mlp.init(seed, scale=0.7)
+    th = scenes.mlp_init(seed, scale=0.7)
     th[mlp.NPARAMS - 5:] = np.random.default_rng(seed).normal(size=5) * 0.1  # nonzero b3
     loss, g = mlp.loss_grad(th, X, y)
     rng = np.random.default_rng(seed + 10)
@@ -63,7 +64,7 @@ def test_bf16_rounding_values():
 
 def test_bf16_mode_is_close_to_fp64_and_training_learns():
     X, y = _data(5, n=200)
-    th = mlp.init(5, scale=0.5)
+    th = scenes.mlp_init(5, scale=0.5)
     l64, g64 = mlp.loss_grad(th, X, y)
     l16, g16 = mlp.loss_grad(th, X, y, bf16=True)
     assert abs(l16 - l64) < 2e-2 * l64

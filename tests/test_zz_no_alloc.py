@@ -73,7 +73,58 @@ def test_static_flux_rejects_sizes_beyond_its_scratch():
     st = air.lib().air_band_flux_static(C.c_void_p(J.data_ptr()), 1 << 32, 2, None, None, 1 << 31,
                                         1.0, C.c_void_p(out.data_ptr()), None)
     assert st == air.AIR_ERR_ARG
+    # n valid, only the stride out of range: (n_bands - 1) * stride overflows int64
+    st = air.lib().air_band_flux_static(C.c_void_p(J.data_ptr()), 1 << 62, 3, None, None, 8,
+                                        1.0, C.c_void_p(out.data_ptr()), None)
+    assert st == air.AIR_ERR_ARG
+    assert b"overflows" in air.lib().air_last_error()
     host = np.zeros((2, 8), dtype=np.float32)
     st = air.lib().air_band_flux_static(C.c_void_p(host.ctypes.data), 8, 2, None, None, 8, 1.0,
                                         C.c_void_p(out.data_ptr()), None)
     assert st == air.AIR_ERR_ARG
+
+
+def test_static_flux_levels_up_to_the_render_maximum():
+    """Levels 0..20 (every level a render can produce) scale by exactly 4^-L;
+    a counted level outside that range turns the flux into NaN instead of a
+    silently wrong power of two."""
+    air.build()
+    n = 21 * 40
+    g = torch.Generator().manual_seed(3)
+    I = torch.rand((2, n), generator=g, dtype=torch.float32).cuda()
+    lev = torch.arange(n, dtype=torch.int32).remainder(21).cuda()
+    leaf = torch.ones(n, dtype=torch.uint8).cuda()
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    assert _call(I, n, 0.75, lev, leaf, out) == air.AIR_OK
+    torch.cuda.synchronize()
+    ref = (I.cpu().double().numpy() * 0.75 * 4.0 ** -lev.cpu().double().numpy()).sum(axis=1)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-12, atol=0)
+    for bad in (21, -1):
+        lev2 = lev.clone()
+        lev2[7] = bad
+        assert _call(I, n, 0.75, lev2, leaf, out) == air.AIR_OK
+        torch.cuda.synchronize()
+        assert np.isnan(out.cpu().numpy()).all(), bad
+        leaf2 = leaf.clone()
+        leaf2[7] = 0  # not counted: the bad level is ignored
+        assert _call(I, n, 0.75, lev2, leaf2, out) == air.AIR_OK
+        torch.cuda.synchronize()
+        assert np.isfinite(out.cpu().numpy()).all(), bad
+
+
+def test_static_flux_binding_checks_layout():
+    air.build()
+    I = torch.zeros((2, 8), dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):
+        air.band_flux_static(I.double(), 8, 1.0)
+    with pytest.raises(ValueError):
+        air.band_flux_static(I.t().contiguous().t(), 8, 1.0)
+    with pytest.raises(ValueError):
+        air.band_flux_static(I, 9, 1.0)
+    with pytest.raises(ValueError):
+        air.band_flux_static(I, 8, 1.0, level=torch.zeros(8, dtype=torch.int64, device="cuda"))
+    with pytest.raises(ValueError):
+        air.band_flux_static(I, 8, 1.0, is_leaf=torch.ones(4, dtype=torch.uint8, device="cuda"))
+    out = air.band_flux_static(I, 8, 1.0, level=torch.zeros(8, dtype=torch.int32, device="cuda"))
+    torch.cuda.synchronize()
+    assert (out.cpu().numpy() == 0.0).all()
