@@ -132,7 +132,7 @@ typedef struct {
   int32_t tile_w;                 /* fixed images: a warp traces tile_w x (32 / tile_w)
                                      pixels (1, 2, 4, 8, 16, 32; default 8) */
   int32_t bands_per_thread;       /* single-view renders: bands one thread carries
-                                     along a ray (1, 2, 4, 8, 16; default all up to 16) */
+                                     along a ray (1, 2, 4, 8, 16; default: all of them up to 8 bands, else 8) */
   int32_t batch_bands_per_thread; /* batched renders (default 8 for more than 4 bands) */
   int32_t batch_blocks_per_sm;    /* persistent CTAs per SM of batched renders
                                      (default: as many as fit) */
@@ -191,6 +191,41 @@ typedef struct {
 AIR_API air_status air_render_batch(air_grid *g, const air_view *views, int32_t n_views,
                                     const air_params *params, const air_batch_opts *opts,
                                     air_image *outs);
+
+/* ---- One image over several processes (Section 2, parallelisation) ---------
+ * The paper distributes the pixels of each ray-tracing sweep over the
+ * processors and gathers the traced values for the refinement check. Here
+ * every process (rank) holds the grid and runs the refinement itself on the
+ * gathered values, so all ranks build the same quadtree: the new rays of each
+ * sweep, nodes [first, first + count) in creation order, are split into
+ * `world` contiguous slices, rank r traces nodes
+ * [first + count r / world, first + count (r + 1) / world), and `exchange` is
+ * called to fill in the other ranks' slices.
+ * exchange(user, first, count, n_bands, coldens, intensity, stride, p, steps):
+ *   the arrays are device memory of the library's quadtree (node k at
+ *   coldens[k], intensity[b * stride + k], p[k], steps[k]); on entry this
+ *   rank's slice is complete (the handle's stream has been synchronised), on
+ *   return every node of [first, first + count) must hold its traced values,
+ *   written or queued on the handle's stream. Return 0, or nonzero to abort
+ *   the render (AIR_ERR_ARG). It is called once per sweep, the base image
+ *   included, on the calling thread. */
+typedef int32_t (*air_exchange_fn)(void *user, int64_t first, int64_t count, int32_t n_bands,
+                                   float *coldens, float *intensity, int64_t stride, float *p,
+                                   uint32_t *steps);
+typedef struct {
+  int32_t rank, world;      /* 0 <= rank < world */
+  air_exchange_fn exchange; /* required when world > 1 */
+  void *user;
+} air_shard;
+
+/* air_render_adaptive with the rays of every sweep split over `world` ranks
+ * (see air_shard). Every rank must make the same call (same grid contents,
+ * view and params); each returns the whole image, bitwise equal to
+ * air_render_adaptive's. Errors: as air_render_adaptive; AIR_ERR_ARG for a
+ * bad rank / world, a missing exchange, or an exchange that failed. */
+AIR_API air_status air_render_adaptive_sharded(air_grid *g, const air_view *view,
+                                               const air_params *params, const air_shard *shard,
+                                               air_image *out);
 
 /* ---- Learned refinement-depth proposal (not in the paper) ------------------
  * A perceptron 16 -> 64 -> 64 -> 5 (ReLU) with BF16 weights and activations and

@@ -39,7 +39,7 @@ EXPORTED = ["air_load_grid", "air_set_stream", "air_render_fixed", "air_render_a
             "air_learn_samples", "air_render_learned", "air_autotune", "air_set_tuning",
             "air_get_tuning",
             "air_profile_enable", "air_profile_read", "air_band_flux_static", "air_render_raster",
-            "air_render_adaptive_spectra",
+            "air_render_adaptive_spectra", "air_render_adaptive_sharded",
             "air_free",
             "air_last_error", "air_version"]
 PHASES = ("march", "scan", "balance", "refine", "output", "batch", "learn")
@@ -106,6 +106,25 @@ class Params(C.Structure):
     _fields_ = [("base_res", C.c_int32), ("max_level", C.c_int32), ("xi_crit", C.c_double),
                 ("xi_norm", C.c_int32), ("refine_on", C.c_int32), ("fp64_level", C.c_int32),
                 ("include_interior", C.c_int32)]
+
+
+EXCHANGE_FN = C.CFUNCTYPE(C.c_int32, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p,
+                          C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p)
+
+
+class Shard(C.Structure):
+    _fields_ = [("rank", C.c_int32), ("world", C.c_int32), ("exchange", EXCHANGE_FN),
+                ("user", C.c_void_p)]
+
+
+class _DeviceArray:
+    """A view of library-owned device memory for torch.as_tensor (CUDA array
+    interface, no copy)."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
 
 
 class BatchOpts(C.Structure):
@@ -203,6 +222,9 @@ def lib():
             L.air_band_flux_static.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
                                                C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
                                                C.c_void_p]
+            L.air_render_adaptive_sharded.restype = C.c_int
+            L.air_render_adaptive_sharded.argtypes = [C.c_void_p, C.POINTER(View), C.POINTER(Params),
+                                                      C.POINTER(Shard), C.POINTER(Image)]
             L.air_render_adaptive_spectra.restype = C.c_int
             L.air_render_adaptive_spectra.argtypes = [C.c_void_p, C.POINTER(View), C.POINTER(Params),
                                                       C.POINTER(Image), C.c_void_p, C.c_int64]
@@ -489,6 +511,51 @@ class Grid:
         _check(st)
         self._cap_hint = max(self._cap_hint, int(im.n_out))
         self._raster_src = (int(base_res), int(max_level))
+        return self._result(im, out)
+
+    def render_adaptive_sharded(self, view, base_res, max_level, xi_crit, group=None, xi_norm=0,
+                                refine_on=0, fp64_level=-1, include_interior=False, mem="device",
+                                fields=ALL, capacity=None):
+        """air_render_adaptive_sharded over the torch.distributed group: this
+        rank traces its slice of every sweep's rays, the slices are exchanged
+        (shard.exchange_slices), and every rank returns the whole image."""
+        import torch
+        import torch.distributed as dist
+        from . import shard as _shard
+        rank, world = dist.get_rank(group), dist.get_world_size(group)
+        errors = []
+
+        def exchange(user, first, count, nb, N, I, stride, p, steps):
+            try:
+                arrs = [torch.as_tensor(_DeviceArray(N + 4 * first, count, "<f4"), device="cuda"),
+                        torch.as_tensor(_DeviceArray(p + 4 * first, count, "<f4"), device="cuda"),
+                        torch.as_tensor(_DeviceArray(steps + 4 * first, count, "<i4"), device="cuda")]
+                arrs += [torch.as_tensor(_DeviceArray(I + 4 * (b * stride + first), count, "<f4"),
+                                         device="cuda") for b in range(nb)]
+                _shard.exchange_slices(arrs, rank, world, group)
+                torch.cuda.current_stream().synchronize()
+                return 0
+            except Exception as e:  # reported after the call returns
+                errors.append(e)
+                return 1
+
+        cb = EXCHANGE_FN(exchange)
+        sh = Shard(rank, world, cb, None)
+        _check(lib().air_set_stream(self._h, _stream()))
+        p = Params(int(base_res), int(max_level), float(xi_crit), int(xi_norm), int(refine_on),
+                   int(fp64_level), 1 if include_interior else 0)
+        cap = capacity or max(self._cap_hint, 4 * base_res * base_res)
+        for _ in range(2):
+            im, out = self._alloc(cap, mem, fields)
+            st = lib().air_render_adaptive_sharded(self._h, C.byref(_view(view)), C.byref(p),
+                                                   C.byref(sh), C.byref(im))
+            if errors:
+                raise errors[0]
+            if st != AIR_ERR_CAPACITY:
+                break
+            cap = int(im.n_out)
+        _check(st)
+        self._cap_hint = max(self._cap_hint, int(im.n_out))
         return self._result(im, out)
 
     def render_adaptive_spectra(self, view, base_res, max_level, xi_crit, xi_norm=0, refine_on=0,

@@ -291,7 +291,7 @@ air_status render_fixed(air_grid *g, const air_view *view, int32_t res, int32_t 
   src.tile_w = g->tune.tile_w > 0 ? g->tune.tile_w : 8;
   RayOut ro{w.fN, w.fI, n, w.fsteps, w.fp};
   g->prof.used = 0;
-  CU_TRY(prof_open(g, AIR_PHASE_MARCH, nb > (g->tune.bands_per_thread > 0 ? g->tune.bands_per_thread : 16) ? 2 : 1));
+  CU_TRY(prof_open(g, AIR_PHASE_MARCH, nb > (g->tune.bands_per_thread > 0 ? g->tune.bands_per_thread : default_bands_per_thread(nb)) ? 2 : 1));
   CU_TRY(launch_march(g->gv, cam, src, ro, march_tune(g, fp64_level), st));
   CU_TRY(prof_close(g));
   FluxArgs fa{};
@@ -311,11 +311,18 @@ air_status render_fixed(air_grid *g, const air_view *view, int32_t res, int32_t 
 }
 
 air_status render_adaptive(air_grid *g, const air_view *view, const air_params *pr, air_image *im,
-                           float *spectra, int64_t spectra_cap) {
+                           float *spectra, int64_t spectra_cap, const air_shard *shard) {
   g->raster.ok = false;  // the workspace tree is about to change
   air_status s = check_image(im);
   if (s) return s;
   const bool streamed = spectra != nullptr;
+  const bool sharded = shard != nullptr && shard->world > 1;
+  if (shard) {
+    if (shard->world < 1 || shard->rank < 0 || shard->rank >= shard->world)
+      return set_error(AIR_ERR_ARG, "shard needs 0 <= rank < world");
+    if (sharded && !shard->exchange) return set_error(AIR_ERR_ARG, "shard->exchange is NULL");
+    if (sharded && streamed) return set_error(AIR_ERR_ARG, "sharded renders do not stream spectra");
+  }
   const float *spectra_dev = nullptr;
   if (streamed) {
     if (!pr || pr->include_interior != 1)
@@ -379,6 +386,25 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
       ro.stride = src.count;
       ro.ioff = src.first;
     }
+    if (sharded) {
+      // this rank's slice of the sweep's rays, then the other slices from
+      // the other ranks (Section 2: trace distributed, gather for the scan)
+      const int64_t first = src.first, count = src.count;
+      const int64_t lo = count * shard->rank / shard->world;
+      const int64_t hi = count * (shard->rank + 1) / shard->world;
+      src.first = first + lo;
+      src.count = hi - lo;
+      if (src.count > 0) {
+        CU_TRY(prof_open(g, AIR_PHASE_MARCH, launches));
+        CU_TRY(launch_march(g->gv, cam, src, ro, tune, g->stream));
+        CU_TRY(prof_close(g));
+      }
+      CU_TRY(cudaStreamSynchronize(g->stream));
+      if (shard->exchange(shard->user, first, count, nb, tv.N, tv.I, tv.cap, tv.p, tv.steps) != 0)
+        return set_error(AIR_ERR_ARG, "shard exchange failed (sweep rays %lld..%lld)", (long long)first,
+                         (long long)(first + count));
+      return AIR_OK;
+    }
     CU_TRY(prof_open(g, AIR_PHASE_MARCH, launches));
     CU_TRY(launch_march(g->gv, cam, src, ro, tune, g->stream));
     CU_TRY(prof_close(g));
@@ -407,11 +433,23 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
   } else {
     g->last.valid = false;
     const int64_t nbase = (int64_t)n0 * n0;
-    if ((s = ensure_nodes(g, std::min<int64_t>(bound, std::max<int64_t>(4 * nbase, w.cap)), 0, bound, !streamed))) return s;
+    // The sweep loop keeps its counts on the device when the node arrays can
+    // be sized for the whole image pyramid at once (no growth mid-loop); a
+    // render whose pyramid would take more than half of the free device
+    // memory reads the counts back sweep by sweep and grows on demand.
+    bool dev_loop = !streamed && !sharded;
+    if (dev_loop && !(w.cap >= bound && w.n_bands == nb)) {
+      size_t fr = 0, tot = 0;
+      CU_TRY(cudaMemGetInfo(&fr, &tot));
+      const double need = (double)bound * (31.0 + 4.0 * nb) - (double)w.cap * (31.0 + 4.0 * nb);
+      dev_loop = need <= 0.5 * (double)fr;
+    }
+    if ((s = ensure_nodes(g, dev_loop ? bound : std::min<int64_t>(bound, std::max<int64_t>(4 * nbase, w.cap)),
+                          0, bound, !streamed))) return s;
     t = w.tree(n0, Lm);
     const MarchTune tune = march_tune(g, pr->fp64_level);
     g->prof.used = 0;
-    const int nbt_eff = tune.nbt > 0 ? tune.nbt : (nb < 16 ? nb : 16);
+    const int nbt_eff = tune.nbt > 0 ? tune.nbt : default_bands_per_thread(nb);
     const int march_launches = nb > nbt_eff ? 2 : 1;  // march (+ band sum when bands are chunked)
     // step i + ii: base image
     CU_TRY(prof_open(g, AIR_PHASE_REFINE, 1));
@@ -426,14 +464,87 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
     int cur = 0;
     int64_t m = Lm > 0 ? nbase : 0;
     CU_TRY(launch_list_init(w.open[0], m, st));
+    // level maps (levels 1 .. Lm - 1) for the stencil and balance lookups,
+    // unless they would take more than a quarter of the free device memory
+    int32_t *lmap = nullptr;
+    const size_t map_bytes = sizeof(int32_t) * (size_t)level_map_offset(n0, Lm);
+    if (map_bytes > 0) {
+      bool fits = w.lmap_b >= map_bytes;
+      if (!fits) {
+        size_t fr = 0, tot = 0;
+        CU_TRY(cudaMemGetInfo(&fr, &tot));
+        fits = (double)map_bytes <= 0.25 * (double)fr;
+        if (fits) CU_TRY(ensure((void **)&w.lmap, &w.lmap_b, map_bytes));
+      }
+      if (fits) {
+        lmap = w.lmap;
+        CU_TRY(cudaMemsetAsync(lmap, 0xff, map_bytes, st));
+      }
+    }
+    if (dev_loop) {
+      // Steps iii-v with every count on the device: each sweep's kernels read
+      // the open-list length, the flag count and the node count from the
+      // device state, so the host queues sweep after sweep without waiting.
+      // It reads the state back two sweeps behind, only to learn that the
+      // loop has ended; the (at most two) sweeps queued past the end find
+      // `done` set and do nothing.
+      if (!w.d_sweep) CU_TRY(cudaMalloc((void **)&w.d_sweep, sizeof(SweepState)));
+      if (!w.h_sweep) CU_TRY(cudaMallocHost((void **)&w.h_sweep, 3 * sizeof(SweepState)));
+      for (int k = 0; k < 2; ++k)
+        if (!w.ev_sweep[k]) CU_TRY(cudaEventCreateWithFlags(&w.ev_sweep[k], cudaEventDisableTiming));
+      SweepState &s0 = w.h_sweep[2];
+      std::memset(&s0, 0, sizeof(SweepState));
+      s0.n = nbase;
+      s0.m = m;
+      s0.done = m == 0;
+      CU_TRY(cudaMemcpyAsync(w.d_sweep, &s0, sizeof(SweepState), cudaMemcpyHostToDevice, st));
+      // the fused scan and balance only set flags: the base pixels' start at zero
+      CU_TRY(cudaMemsetAsync(w.flag, 0, sizeof(uint32_t) * (size_t)nbase, st));
+      int32_t *const open2[2] = {w.open[0], w.open[1]};
+      const int64_t nb_cap = scan_blocks(open_max);
+      RaySource ds{};
+      ds.mode = 2; ds.n0 = n0; ds.lvl = t.lvl; ds.pi = t.pi; ds.pj = t.pj; ds.sweep = w.d_sweep;
+      constexpr int kAhead = 2;
+      // every sweep refines at least one pixel
+      const int64_t max_sweeps = (bound - nbase) / 4 + kAhead + 1;
+      int64_t q = 0;
+      for (;; ++q) {
+        if (q >= kAhead) {
+          CU_TRY(cudaEventSynchronize(w.ev_sweep[q % kAhead]));
+          if (w.h_sweep[q % kAhead].done) break;
+        }
+        if (q > max_sweeps) return set_error(AIR_ERR_NUMERIC, "sweep loop did not end");
+        // step iii: scan and balance in one pass (counted as the scan phase)
+        CU_TRY(prof_open(g, AIR_PHASE_SCAN, 1));
+        CU_TRY(launch_sweep_scan_balance(t, open2, w.d_sweep, pr->xi_crit, pr->xi_norm, pr->refine_on,
+                                         w.flag, w.d_err, st, lmap));
+        CU_TRY(prof_close(g));
+        CU_TRY(prof_open(g, AIR_PHASE_REFINE, 3));
+        CU_TRY(launch_sweep_count(t, open2, w.d_sweep, w.flag, w.bcount, w.boff, nb_cap, st));
+        CU_TRY(launch_sweep_emit(t, open2, w.d_sweep, w.flag, w.boff, nb_cap, st, lmap));
+        CU_TRY(prof_close(g));
+        // step ii on the new pixels; the march's last block (or the band sum
+        // after it) moves the state on to the next sweep
+        if ((s = march_nodes(t, ds, tune, march_launches))) return s;
+        CU_TRY(cudaMemcpyAsync(&w.h_sweep[q % kAhead], w.d_sweep, sizeof(SweepState),
+                               cudaMemcpyDeviceToHost, st));
+        CU_TRY(cudaEventRecord(w.ev_sweep[q % kAhead], st));
+      }
+      CU_TRY(cudaStreamSynchronize(st));
+      const SweepState &fin = w.h_sweep[(q - 1) % kAhead];
+      n = fin.n;
+      n_refined = fin.n_refined;
+      sweeps = fin.sweeps;
+      m = 0;
+    }
     for (;;) {
       if (m == 0) break;  // no leaf below the top level: nothing can be flagged
       // step iii: scan, then balance; count the flags and the next list
       CU_TRY(prof_open(g, AIR_PHASE_SCAN, 1));
-      CU_TRY(launch_list_scan(t, w.open[cur], m, pr->xi_crit, pr->xi_norm, pr->refine_on, w.flag, st));
+      CU_TRY(launch_list_scan(t, w.open[cur], m, pr->xi_crit, pr->xi_norm, pr->refine_on, w.flag, st, lmap));
       CU_TRY(prof_close(g));
       CU_TRY(prof_open(g, AIR_PHASE_BALANCE, 1));
-      CU_TRY(launch_list_balance(t, w.open[cur], m, w.flag, w.d_err, st));
+      CU_TRY(launch_list_balance(t, w.open[cur], m, w.flag, w.d_err, st, lmap));
       CU_TRY(prof_close(g));
       CU_TRY(prof_open(g, AIR_PHASE_REFINE, 2));
       CU_TRY(launch_list_count(t, w.open[cur], m, w.flag, w.bcount, w.boff, w.d_total, st));
@@ -452,7 +563,7 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
       }
       // step iv: refine (and the next open-leaf list), then step ii on the new pixels
       CU_TRY(prof_open(g, AIR_PHASE_REFINE, 1));
-      CU_TRY(launch_list_emit(t, w.open[cur], m, w.flag, w.boff, w.d_total, n, w.open[cur ^ 1], st));
+      CU_TRY(launch_list_emit(t, w.open[cur], m, w.flag, w.boff, w.d_total, n, w.open[cur ^ 1], st, lmap));
       CU_TRY(prof_close(g));
       src.lvl = t.lvl; src.pi = t.pi; src.pj = t.pj; src.first = n; src.count = 4 * nflag;
       if ((s = march_nodes(t, src, tune, march_launches))) return s;
@@ -568,6 +679,14 @@ air_status air_render_adaptive(air_grid *g, const air_view *view, const air_para
   air::g_err[0] = 0;
   if (!g) return air::set_error(AIR_ERR_ARG, "grid is NULL");
   return air::render_adaptive(g, view, params, out);
+}
+
+air_status air_render_adaptive_sharded(air_grid *g, const air_view *view, const air_params *params,
+                                       const air_shard *shard, air_image *out) {
+  air::g_err[0] = 0;
+  if (!g) return air::set_error(AIR_ERR_ARG, "grid is NULL");
+  if (!shard) return air::set_error(AIR_ERR_ARG, "shard is NULL");
+  return air::render_adaptive(g, view, params, out, nullptr, 0, shard);
 }
 
 air_status air_render_adaptive_spectra(air_grid *g, const air_view *view, const air_params *params,

@@ -225,10 +225,10 @@ __global__ void __launch_bounds__(kBatchBlock) k_air_batch(BatchArgs a) {
     }
     // step iii: scan, then balance
     for (int64_t k = gtid; k < n; k += gstride)
-      a.flag[k] = xi_flag(t, (int)(a.view[k] * nn0), k, a.xi_crit, a.xi_norm, a.refine_on);
+      a.flag[k] = xi_flag(t, NodeLookup{(int)(a.view[k] * nn0), nullptr}, k, a.xi_crit, a.xi_norm, a.refine_on);
     if (!grid_sync(a.ctl, nblk, a.timeout_ns)) return;
     for (int64_t k = gtid; k < n; k += gstride)
-      if (a.flag[k]) balance_from(t, (int)(a.view[k] * nn0), (int)k, a.flag, &a.ctl->err);
+      if (a.flag[k]) balance_from(t, NodeLookup{(int)(a.view[k] * nn0), nullptr}, (int)k, a.flag, &a.ctl->err);
     if (!grid_sync(a.ctl, nblk, a.timeout_ns)) return;
     // step iv: per-view prefix sum over static node ranges
     const int64_t per = (n + nblk - 1) / nblk;
@@ -447,7 +447,9 @@ static bool batch_fns(int nbt, bool amr, int fmt, BatchOccFn *occ, BatchLaunchFn
   return false;
 }
 
-static int default_bands_per_thread(int nb) {
+// Bands per thread of batched renders when the tuning leaves it open: the
+// template width that holds every band, up to 8.
+static int default_batch_bands_per_thread(int nb) {
   if (nb <= 1) return 1;
   if (nb <= 2) return 2;
   if (nb <= 4) return 4;
@@ -475,7 +477,7 @@ air_status render_batch(air_grid *g, const air_view *views, int32_t V, const air
   if (!(op.wait_timeout_ms > 0.0)) op.wait_timeout_ms = 2000.0;
   const int nb = g->gv.n_bands;
   int nbt = op.bands_per_thread > 0 ? op.bands_per_thread
-            : (g->tune.batch_bands_per_thread > 0 ? g->tune.batch_bands_per_thread : default_bands_per_thread(nb));
+            : (g->tune.batch_bands_per_thread > 0 ? g->tune.batch_bands_per_thread : default_batch_bands_per_thread(nb));
   if (g->gv.cell_fmt == kCellLam && nbt > 0) nbt = 1;  // one band
   BatchOccFn occ;
   BatchLaunchFn launch;

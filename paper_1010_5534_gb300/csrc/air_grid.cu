@@ -192,10 +192,18 @@ void free_grid_impl(air_grid *g) {
   dfree(w.view);
   dfree(w.lvl); dfree(w.pi); dfree(w.pj); dfree(w.child); dfree(w.N); dfree(w.I); dfree(w.p);
   dfree(w.steps); dfree(w.flag); dfree(w.bcount); dfree(w.boff); dfree(w.d_total); dfree(w.d_err);
-  dfree(w.open[0]); dfree(w.open[1]);
+  dfree(w.open[0]); dfree(w.open[1]); dfree(w.lmap);
+  w.lmap_b = 0;
   dfree(w.partial); dfree(w.d_flux); dfree(w.fN); dfree(w.fI); dfree(w.fp); dfree(w.fsteps);
   dfree(w.o_level); dfree(w.o_i); dfree(w.o_j); dfree(w.o_leaf); dfree(w.o_N); dfree(w.o_p);
   dfree(w.o_I);
+  dfree(w.d_sweep);
+  if (w.h_sweep) cudaFreeHost(w.h_sweep);
+  w.h_sweep = nullptr;
+  for (int k = 0; k < 2; ++k) {
+    if (w.ev_sweep[k]) cudaEventDestroy(w.ev_sweep[k]);
+    w.ev_sweep[k] = nullptr;
+  }
   if (w.h_total) cudaFreeHost(w.h_total);
   if (w.h_err) cudaFreeHost(w.h_err);
   if (w.h_flux) cudaFreeHost(w.h_flux);

@@ -29,6 +29,8 @@ struct Workspace {
   size_t bcount_b = 0, boff_b = 0;
   int64_t *d_total = nullptr;  // [3]
   int32_t *open[2] = {nullptr, nullptr};  // open-leaf lists (ping-pong)
+  int32_t *lmap = nullptr;                 // level maps of the single-view tree
+  size_t lmap_b = 0;
   size_t open_b[2] = {0, 0};
   uint32_t *d_err = nullptr;
   double *partial = nullptr;
@@ -43,6 +45,11 @@ struct Workspace {
   uint8_t *o_leaf = nullptr;
   float *o_N = nullptr, *o_p = nullptr, *o_I = nullptr;
   size_t o_level_b = 0, o_i_b = 0, o_j_b = 0, o_leaf_b = 0, o_N_b = 0, o_p_b = 0, o_I_b = 0;
+  // sweep loop with counts on the device: its state, pinned copies of it
+  // (two in flight, one for the initial state) and the copies' events
+  SweepState *d_sweep = nullptr;
+  SweepState *h_sweep = nullptr;  // [3]
+  cudaEvent_t ev_sweep[2] = {nullptr, nullptr};
   // pinned host scalars
   int64_t *h_total = nullptr;  // [3]
   uint32_t *h_err = nullptr;
@@ -201,8 +208,10 @@ air_status ensure_nodes(air_grid *g, int64_t need, int64_t keep, int64_t bound, 
 air_status render_batch(air_grid *g, const air_view *views, int32_t n_views,
                         const air_params *params, const air_batch_opts *opts, air_image *outs);
 // spectra (page-locked host, [n_bands][spectra_cap]) set: streamed spectra.
+// shard set: the rays of every sweep split over ranks (air_render_adaptive_sharded).
 air_status render_adaptive(air_grid *g, const air_view *view, const air_params *pr, air_image *im,
-                           float *spectra = nullptr, int64_t spectra_cap = 0);
+                           float *spectra = nullptr, int64_t spectra_cap = 0,
+                           const air_shard *shard = nullptr);
 // Step vi on the quadtree of nodes [0, n) in the workspace; with spectra_dev
 // set, the band intensities are read from there (stride spectra_cap).
 air_status output_tree(air_grid *g, const Camera &cam, const air_params *pr, air_image *im,

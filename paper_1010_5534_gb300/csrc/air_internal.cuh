@@ -49,16 +49,22 @@ struct Camera {
   double H;
 };
 
-// Ray list: either explicit nodes (level, i, j) of an n0 base image, or the
-// implicit pixels of a res x res fixed image.
+struct SweepState;
+
+// Ray list: explicit nodes (level, i, j) of an n0 base image, the implicit
+// pixels of a res x res fixed image, or the new nodes of a sweep whose count
+// stays on the device.
 struct RaySource {
-  int mode;             // 0 nodes, 1 fixed grid
+  int mode;             // 0 nodes, 1 fixed grid, 2 nodes counted on the device
   int n0;               // base resolution (nodes) or res (grid)
   const int8_t *lvl;
   const int32_t *pi, *pj;
-  int64_t first, count; // rays [first, first + count) of the list / image
+  int64_t first, count; // rays [first, first + count) of the list / image (modes 0, 1)
   int tile_w;           // grid mode: a warp covers tile_w x (32 / tile_w) pixels
   const int32_t *list;  // nodes mode: if set, ray r is node list[r] (first ignored)
+  SweepState *sweep;    // mode 2: rays [S->n, S->n + 4 S->tot[0]), none once S->done;
+                        // blocks take 128-ray chunks from S->ray_ctr[band chunk]
+  int advance;          // mode 2: the launch's last block moves S on to the next sweep
 };
 
 struct RayOut {
@@ -76,7 +82,7 @@ struct RayOut {
 struct MarchTune {
   int block;            // threads per block
   int fp64_level;       // bricks at this level or deeper use FP64 entry/exit
-  int nbt;              // bands one thread carries (1, 2, 4, 8, 16; 0 = all up to 16)
+  int nbt;              // bands one thread carries (1, 2, 4, 8, 16; 0 = all up to 8, else 8)
 };
 
 // Kahan-compensated sum: s += x with running compensation c.
@@ -112,6 +118,8 @@ int sm_count();
 
 cudaError_t launch_march(const GridView &g, const Camera &cam, const RaySource &src,
                          const RayOut &out, const MarchTune &tune, cudaStream_t st);
+// Bands one thread carries when the tuning leaves it open (launch_march).
+inline int default_bands_per_thread(int n_bands) { return n_bands <= 8 ? n_bands : 8; }
 cudaError_t launch_band_sum(const float *I, int n_bands, int64_t stride, int64_t first,
                             int64_t count, float *p, cudaStream_t st, int64_t ioff = 0);
 

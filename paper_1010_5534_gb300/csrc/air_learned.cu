@@ -303,7 +303,7 @@ static air_status base_and_features(air_grid *g, const Camera &cam, const air_pa
   src.mode = 0; src.n0 = n0; src.lvl = t.lvl; src.pi = t.pi; src.pj = t.pj; src.first = 0; src.count = nbase;
   RayOut ro{t.N, t.I, t.cap, t.steps, t.p, lw.tau0, lw.maxlev};
   const MarchTune tune = march_tune(g, pr->fp64_level);
-  CU_TRY(prof_open(g, AIR_PHASE_MARCH, g->gv.n_bands > (tune.nbt > 0 ? tune.nbt : 16) ? 2 : 1));
+  CU_TRY(prof_open(g, AIR_PHASE_MARCH, g->gv.n_bands > (tune.nbt > 0 ? tune.nbt : default_bands_per_thread(g->gv.n_bands)) ? 2 : 1));
   CU_TRY(launch_march(g->gv, cam, src, ro, tune, st));
   CU_TRY(prof_close(g));
   CU_TRY(prof_open(g, AIR_PHASE_LEARN, 2));
@@ -414,7 +414,7 @@ air_status render_learned(air_grid *g, const air_view *view, const air_params *p
   CU_TRY(cudaGetLastError());
   CU_TRY(prof_close(g));
   const MarchTune tune = march_tune(g, pr->fp64_level);
-  const int march_launches = nb > (tune.nbt > 0 ? tune.nbt : 16) ? 2 : 1;
+  const int march_launches = nb > (tune.nbt > 0 ? tune.nbt : default_bands_per_thread(nb)) ? 2 : 1;
   if (P > 0) {
     // the proposal wave: every pixel of every proposed subtree
     RaySource ps{};

@@ -56,6 +56,7 @@ struct BandRegs {
   float kap[NBT];  // kappa_b
   float ik[NBT];   // 1 / kappa_b (0 where kappa_b = 0)
   float nk[NBT];   // -kappa_b log2(e): T_b = 2^(nk_b N)
+  float kmax;      // largest kappa_b of the chunk
 };
 
 // Per-band registers of bands [b0, b0 + nbh) (zero beyond).
@@ -68,6 +69,9 @@ __device__ __forceinline__ void band_regs(BandRegs<NBT> &br, const float *kappa,
     br.ik[b] = b < nbh ? __ldg(invkappa + b0 + b) : 0.f;
     br.nk[b] = (float)(-(double)br.kap[b] * 1.4426950408889634);
   }
+  br.kmax = 0.f;
+#pragma unroll
+  for (int b = 0; b < NBT; ++b) br.kmax = fmaxf(br.kmax, br.kap[b]);
 }
 
 // 2^x by the hardware approximation (PTX ex2.approx.ftz.f32).
@@ -91,19 +95,25 @@ __device__ __forceinline__ void rt_init(RTState<NBT> &r) {
   }
 }
 
-// One cell chord of length ds >= 0 (a zero-length chord, where the ray grazes
-// an edge or corner, adds nothing and is not counted as a step): density rho,
-// and aux = Lambda (kCellLam, as float bits) or the table coordinate of T
-// (kCellXq). With dtau = 0 (kappa_b = 0 or rho = 0) the Taylor form gives the
-// optically thin term j ds T exactly, so no separate case is needed. Both
-// forms of the cell term are evaluated and one is selected, which keeps the
-// march loop free of divergent branches.
-template <int NBT, int FMT>
-__device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t aux, float ds,
+// Transfer step of one cell chord of length ds: density rho, and aux =
+// Lambda (kCellLam, as float bits) or the table coordinate of T (kCellXq).
+// With dtau = 0 (kappa_b = 0 or rho = 0) the series form gives the optically
+// thin term j ds T exactly, so no separate case is needed.
+// THIN = false: both forms of the cell term are evaluated and the one for the
+// cell's dtau is selected, which keeps the loop free of divergent branches.
+// THIN = true: the caller has shown that every band's dtau < 1/4 for this
+// cell, so only the series form is evaluated -- the form the selection would
+// pick, hence the same bits.
+//
+// The products that feed the compensated sums (rho ds, and each form's final
+// product) are rounded explicitly (__fmul_rn), so the compiler cannot fuse
+// them into the sums' subtractions: every instantiation (band chunking, form)
+// rounds alike and gives the same bits.
+template <int NBT, int FMT, bool THIN = false>
+__device__ __forceinline__ void rt_term(RTState<NBT> &r, float rho, uint32_t aux, float ds,
                                         const BandCtx &bc, const BandRegs<NBT> &br) {
-  const float rds = rho * ds;
+  const float rds = __fmul_rn(rho, ds);
   kahan_add(r.N, r.cN, rds);
-  r.steps += ds > 0.f ? 1u : 0u;
   int k = 0;
   float w = 0.f, lam1 = 1.f;
   if (FMT == kCellXq) {
@@ -123,13 +133,28 @@ __device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t aux
       const float dtau = br.kap[b] * rds;
       const float Tn = ex2_approx(br.nk[b] * r.N);
       const float rl = rho * lam;
-      const float t_small = (rl * rds) * (r.T[b] * one_minus_exp_over_x(dtau));
-      const float t_large = (rl * br.ik[b]) * (r.T[b] - Tn);
-      const float term = dtau < 0.25f ? t_small : t_large;
+      const float t_small = __fmul_rn(rl * rds, r.T[b] * one_minus_exp_over_x(dtau));
+      float term = t_small;
+      if (!THIN) {
+        const float t_large = __fmul_rn(rl * br.ik[b], r.T[b] - Tn);
+        term = dtau < 0.25f ? t_small : t_large;
+      }
       r.T[b] = Tn;
       kahan_add(r.I[b], r.cI[b], term);
     }
   }
+}
+
+// One cell chord of length ds >= 0 on the DDA path. A zero-length chord (a
+// ray grazing an edge or corner) adds nothing and is not counted as a step.
+// When kmax (rho ds) < 1/4 every band's dtau is below 1/4 (FP32 rounding is
+// monotonic), so the series form alone gives the bits of the selection.
+template <int NBT, int FMT>
+__device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t aux, float ds,
+                                        const BandCtx &bc, const BandRegs<NBT> &br) {
+  r.steps += ds > 0.f ? 1u : 0u;
+  if (br.kmax * __fmul_rn(rho, ds) < 0.25f) rt_term<NBT, FMT, true>(r, rho, aux, ds, bc, br);
+  else rt_term<NBT, FMT, false>(r, rho, aux, ds, bc, br);
 }
 
 // Cells of a block requested ahead of the march along its dominant axis.
@@ -157,11 +182,61 @@ __device__ __forceinline__ void prefetch_cell(const void *__restrict__ cells, Id
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
-// DDA through a block of nx x ny x nz cells, entered in cell (lx, ly, lz).
-// Q: entry point relative to the low corner of the entry cell (in cells),
-// Dl: direction (cells per unit t), inv = 1 / Dl (0 where Dl = 0), tend:
-// block exit relative to the entry. cells points at the block's cell
-// (0, 0, 0); cell (x, y, z) is record z*sz + y*sy + x.
+// n cells of one column (cell idx, idx + d, ...), every one crossed whole
+// with the same chord ds: the path of a ray parallel to a grid axis, which
+// enters each block of cells through a face and leaves through the opposite
+// one. No DDA is needed. Cells are fetched U at a time (U loads in flight per
+// thread) and the transfer form is chosen per group of U cells: when
+// kmax (rho_max ds) < 1/4 for the group's largest rho, every cell's dtau =
+// kappa_b (rho ds) is below 1/4 too (FP32 rounding is monotonic), and the
+// series form alone gives the bits the per-cell selection would.
+template <int NBT, int FMT, int U, typename Idx>
+__device__ __forceinline__ void march_column(RTState<NBT> &r, const void *__restrict__ cells, Idx idx,
+                                             Idx d, int n, float ds, const BandCtx &bc,
+                                             const BandRegs<NBT> &br) {
+  r.steps += (uint32_t)n;
+  int k = 0;
+  for (; k + U <= n; k += U) {
+    float rh[U];
+    uint32_t xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) load_cell<FMT>(cells, idx + (Idx)u * d, rh[u], xv[u]);
+    idx += (Idx)U * d;
+    float m = rh[0];
+#pragma unroll
+    for (int u = 1; u < U; ++u) m = fmaxf(m, rh[u]);
+    if (br.kmax * (m * ds) < 0.25f) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) rt_term<NBT, FMT, true>(r, rh[u], xv[u], ds, bc, br);
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; ++u) rt_term<NBT, FMT, false>(r, rh[u], xv[u], ds, bc, br);
+    }
+  }
+  for (; k < n; ++k) {
+    float rh;
+    uint32_t xv;
+    load_cell<FMT>(cells, idx, rh, xv);
+    idx += d;
+    rt_term<NBT, FMT, false>(r, rh, xv, ds, bc, br);
+  }
+}
+
+// Cells fetched per group in the column march: 16 in the compiled one-axis
+// form (8 blocks per SM), 8 where the column march runs inside a general
+// kernel (oblique-capable single-view and batched kernels, more registers
+// taken by the 3-axis DDA).
+template <int DIR>
+struct ColumnUnroll {
+  static constexpr int value = DIR >= 1 ? 16 : 8;
+};
+
+// DDA through a block of nx x ny x nz cells, entered in cell (lx, ly, lz),
+// for a ray that moves along two or three grid axes (a ray along one axis
+// takes march_column). Q: entry point relative to the low corner of the
+// entry cell (in cells), Dl: direction (cells per unit t), inv = 1 / Dl (0
+// where Dl = 0), tend: block exit relative to the entry. cells points at the
+// block's cell (0, 0, 0); cell (x, y, z) is record z*sz + y*sy + x.
 //
 // After k steps along axis a the next face of that axis is crossed at
 // t = (k + [Dl > 0] - Q) / Dl = k |inv| + q, evaluated as one fused
@@ -173,80 +248,16 @@ __device__ __forceinline__ void prefetch_cell(const void *__restrict__ cells, Id
 // transfer step, so the load latency overlaps that arithmetic, and the cell
 // kPrefetchAhead steps further along the axis the ray crosses fastest is
 // requested from L1 at every step (clamped into the block), so most loads
-// find their line already on the way (every form but the one-axis throughput
-// form, below). The loop body is straight-line code
+// find their line already on the way. The loop body is straight-line code
 // (the axis to step, the next index and the transfer form are selected, not
-// branched on); its one branch is the exit from the block. A ray parallel to
-// a grid axis takes a one-axis form of the same loop (one boundary parameter,
-// one counter, one bound); the per-launch direction makes this choice the
-// same for every thread.
-// DIR = 1 + A: the launch's rays are all parallel to grid axis A, so only the
-// one-axis form is compiled (fewer registers, more resident warps), without
-// prefetch (the throughput form, for launches of several waves, which are
-// issue-bound); DIR = 4 + A: the same with the prefetch (the latency form,
-// for launches of one wave or less, where every step waits on its cell's
-// load and the prefetch shortens that wait; same arithmetic, so the same
-// results bit for bit); DIR = 0
-// chooses between the one-axis and the 3-axis loop at run time. (A 3-axis-only form was tried
-// for oblique launches: within 1% of DIR = 0 at 56 registers, and at 64 its
-// code ran twice as slow, so it is not kept.)
-template <int NBT, int FMT, typename Idx, int DIR = 0>
+// branched on); its one branch is the exit from the block.
+template <int NBT, int FMT, typename Idx>
 __device__ __forceinline__ void march_block(RTState<NBT> &r, const float Q[3], const float Dl[3],
                                             const float inv[3], float tend, int lx, int ly, int lz,
                                             int nx, int ny, int nz, Idx sy, Idx sz,
                                             const void *__restrict__ cells, const BandCtx &bc,
                                             const BandRegs<NBT> &br) {
-  if (DIR >= 1 || (Dl[0] == 0.f ? (Dl[1] == 0.f) != (Dl[2] == 0.f) : (Dl[1] == 0.f && Dl[2] == 0.f))) {
-    // the ray is parallel to one grid axis (a face-on view): a one-axis DDA
-    const int ax = Dl[0] != 0.f ? 0 : (Dl[1] != 0.f ? 1 : 2);
-    const float D1 = ax == 0 ? Dl[0] : (ax == 1 ? Dl[1] : Dl[2]);
-    const float i1 = ax == 0 ? inv[0] : (ax == 1 ? inv[1] : inv[2]);
-    const float Q1 = ax == 0 ? Q[0] : (ax == 1 ? Q[1] : Q[2]);
-    const int l1 = ax == 0 ? lx : (ax == 1 ? ly : lz);
-    const int n1 = ax == 0 ? nx : (ax == 1 ? ny : nz);
-    const Idx s1 = ax == 0 ? (Idx)1 : (ax == 1 ? sy : sz);
-    const bool pos = D1 > 0.f;
-    const float a1 = fabsf(i1);
-    const float q1 = ((pos ? 1.f : 0.f) - Q1) * i1;
-    const float km = (float)(pos ? n1 - 1 - l1 : l1);
-    const Idx d1 = pos ? s1 : -s1;
-    const Idx plast = (Idx)nz * sz - 1;
-    Idx idx = (Idx)lz * sz + (Idx)ly * sy + (Idx)lx;
-    float rh;
-    uint32_t xv;
-    load_cell<FMT>(cells, idx, rh, xv);
-    // the throughput form (DIR 1..3) runs 14 blocks per SM and is
-    // issue-bound: there the prefetch instructions cost more than they hide
-    constexpr int kAhead = (DIR >= 1 && DIR <= 3) ? 1 : kPrefetchAhead;
-#pragma unroll
-    for (int n = 2; n <= kAhead; ++n) {
-      const Idx pi = idx + (Idx)n * d1;
-      prefetch_cell<FMT>(cells, pi < 0 ? (Idx)0 : (pi > plast ? plast : pi));
-    }
-    float k1 = 0.f, tm = q1, tl = 0.f;
-    for (;;) {
-      const float tn = fminf(tm, tend);
-      const float ds = fmaxf(tn - tl, 0.f);
-      tl = tn;
-      k1 += 1.f;
-      tm = fmaf(k1, a1, q1);
-      const bool more = tn < tend && k1 <= km;
-      idx = more ? idx + d1 : idx;
-      float rh_n;
-      uint32_t xv_n;
-      load_cell<FMT>(cells, idx, rh_n, xv_n);
-      if (kAhead > 1) {
-        const Idx pi = idx + (Idx)kAhead * d1;
-        prefetch_cell<FMT>(cells, pi < 0 ? (Idx)0 : (pi > plast ? plast : pi));
-      }
-      rt_cell<NBT, FMT>(r, rh, xv, ds, bc, br);
-      if (!more) break;
-      rh = rh_n;
-      xv = xv_n;
-    }
-    return;
-  }
-  if constexpr (DIR == 0) {
+  {
   const float INF = FLT_MAX;
   const bool p0 = Dl[0] > 0.f, p1 = Dl[1] > 0.f, p2 = Dl[2] > 0.f;
   const float a0 = fabsf(inv[0]), a1 = fabsf(inv[1]), a2 = fabsf(inv[2]);
@@ -365,7 +376,31 @@ __device__ __forceinline__ bool ray_setup(const GridView &g, const RayGeom &rg, 
 
 __device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
 
-template <int NBT, int FMT, int DIR = 0>
+// ray_setup for a ray along grid axis A: only the two fixed coordinates are
+// needed (the ray enters at the grid face and crosses every cell of its
+// column), computed exactly as ray_setup computes them, so the cells are the
+// same; c[A] is left for the caller. Half of ray_setup's FP64 work, which
+// matters on a GPU whose FP64 rate is a small fraction of FP32's.
+template <int A>
+__device__ __forceinline__ bool axis_ray_setup(const GridView &g, const RayGeom &rg, int L, int i,
+                                               int j, int c[3]) {
+  const double pix = rg.pix0 * exp2_neg(L);
+  const double uc = fma((double)i + 0.5, pix, -rg.H);
+  const double vc = fma((double)j + 0.5, pix, -rg.H);
+  bool hit = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a == A) continue;
+    const double x = fma(vc, rg.V[a], fma(uc, rg.U[a], rg.C[a]));
+    const double q = x * rg.invh[a];
+    const double o = fma(fma(-q, rg.h[a], x), rg.invh[a], q);
+    if (!(o >= 0.0 && o < (double)g.nf[a])) hit = false;
+    c[a] = hit ? (int)o : 0;  // o >= 0: truncation is floor
+  }
+  return hit;
+}
+
+template <int NBT, int FMT>
 __device__ void march_uniform(RTState<NBT> &r, const GridView &g, const double O[3],
                               const RayGeom &rg, double t0, const BandCtx &bc,
                               const BandRegs<NBT> &br) {
@@ -380,7 +415,7 @@ __device__ void march_uniform(RTState<NBT> &r, const GridView &g, const double O
     inv[a] = rg.invDhi[a];
   }
   // the ray leaves through a face of the grid: no end parameter needed
-  march_block<NBT, FMT, int64_t, DIR>(r, Q, Dl, inv, FLT_MAX, lc[0], lc[1], lc[2], g.nf[0], g.nf[1],
+  march_block<NBT, FMT, int64_t>(r, Q, Dl, inv, FLT_MAX, lc[0], lc[1], lc[2], g.nf[0], g.nf[1],
                                  g.nf[2], (int64_t)g.nf[0], (int64_t)g.nf[0] * g.nf[1], g.cells,
                                  bc, br);
 }
@@ -453,7 +488,7 @@ __device__ __forceinline__ int brick_of(const GridView &g, int e, const int c[3]
 // is marched, so its latency overlaps the march. Per-launch constants
 // (direction, its inverse and its double-float split) are read from the
 // kernel-parameter bank, not held per thread.
-template <int NBT, int FMT, int DIR = 0>
+template <int NBT, int FMT>
 __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
                           const RayGeom &rg, double t0, int eax, int fp64_level,
                           const BandCtx &bc, const BandRegs<NBT> &br) {
@@ -563,7 +598,7 @@ __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
     const int64_t boff = (int64_t)code << (3 * lb);
     const void *cb = FMT == kCellRho ? (const void *)((const float *)g.cells + boff)
                                      : (const void *)((const uint2 *)g.cells + boff);
-    march_block<NBT, FMT, int, DIR>(r, Q, Dl, inv, tend, lc[0], lc[1], lc[2], B, B, B, B, B * B, cb,
+    march_block<NBT, FMT, int>(r, Q, Dl, inv, tend, lc[0], lc[1], lc[2], B, B, B, B, B * B, cb,
                                bc, br);
     if (out) break;
     // advance to the exit point
@@ -577,24 +612,31 @@ __device__ void march_amr(RTState<NBT> &r, const GridView &g, const double O[3],
   }
 }
 
-// march_amr for a launch whose rays all run parallel to grid axis A (known at
-// compile time). Such a ray enters the grid, and every brick after, through an
-// A face, and crosses each brick whole: the exit parameter relative to the
-// entry is the brick's width over the direction, S |1/D_A| (in FP64 from the
-// exact width at levels >= fp64_level, else B |1/D_A| in FP32 in the brick's
-// cells), and the other two finest coordinates never change. Every kernel form
-// sends a ray with one moving axis here, so all give the same bits for it.
-// DIR = 1 + A (throughput form) or 4 + A (latency form).
-template <int NBT, int FMT, int DIR>
-__device__ void march_amr_axis(RTState<NBT> &r, const GridView &g, const double O[3],
-                               const RayGeom &rg, double t0, int fp64_level, const BandCtx &bc,
-                               const BandRegs<NBT> &br) {
-  constexpr int A = (DIR - 1) % 3, A1 = (A + 1) % 3, A2 = (A + 2) % 3;
-  const int B = g.B, Lm = g.Lm;
+// A ray parallel to grid axis A (every face-on view: the bench's +z view, the
+// paper's ring view). Such a ray enters the grid, and every brick after,
+// through an A face and crosses each brick whole, through a column of B cells
+// of the brick's level, each with the same chord: the cell width over the
+// direction, |1 / D_A| 2^(Lm - level) (an exact power-of-two scaling of the
+// per-launch FP32 reciprocal). The other two finest coordinates never change
+// and the next brick is the one holding the finest cell just past the far
+// face, so the walk is integer-exact: no entry or exit parameter is computed,
+// in FP32 or FP64, and no cell can be skipped or counted twice. Every kernel
+// form (and the batched kernel) sends such a ray here, so all give the same
+// bits for it. The map entry of the next brick is fetched before the current
+// brick's column is marched, so its latency overlaps the march.
+template <int NBT, int FMT, int A, int U>
+__device__ __forceinline__ void march_amr_axis(RTState<NBT> &r, const GridView &g, int c[3], const RayGeom &rg,
+                               const BandCtx &bc, const BandRegs<NBT> &br) {
+  constexpr int A1 = (A + 1) % 3, A2 = (A + 2) % 3;
+  const int B = g.B, lb = g.log2B, Lm = g.Lm;
   const bool pos = rg.Dhi[A] > 0.f;
-  int c[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) c[a] = clampi((int)floor(O[a] + t0 * rg.D[a]), 0, g.nf[a] - 1);
+  const float a1 = fabsf(rg.invDhi[A]);
+  // cell strides inside a brick, x fastest
+  const int sA = A == 0 ? 1 : (A == 1 ? B : B * B);
+  const int sA1 = A1 == 0 ? 1 : (A1 == 1 ? B : B * B);
+  const int sA2 = A2 == 0 ? 1 : (A2 == 1 ? B : B * B);
+  const int d = pos ? sA : -sA;
+  c[A] = pos ? 0 : g.nf[A] - 1;  // the ray enters through the grid face
   const int max_iter = 4 * g.nf[A];
   int e = map_entry(g, c[0], c[1], c[2]);
   for (int it = 0; it < max_iter; ++it) {
@@ -603,17 +645,6 @@ __device__ void march_amr_axis(RTState<NBT> &r, const GridView &g, const double 
     r.maxlev = max(r.maxlev, lev);
     const int shift = Lm - lev;
     const int S = B << shift;
-    const float up = __int_as_float((127 + shift) << 23);  // 2^shift
-    float Q[3] = {0.f, 0.f, 0.f}, Dl[3] = {0.f, 0.f, 0.f}, inv[3] = {0.f, 0.f, 0.f};
-    Dl[A] = rg.Dhi[A] * __int_as_float((127 - shift) << 23);
-    inv[A] = rg.invDhi[A] * up;
-    Q[A] = pos ? 0.f : 1.f;  // entry face, in the entry cell's frame
-    int lc[3];
-    lc[A] = pos ? 0 : B - 1;
-    lc[A1] = (c[A1] >> shift) & (B - 1);
-    lc[A2] = (c[A2] >> shift) & (B - 1);
-    const float tend = lev >= fp64_level ? (float)((double)S * fabs(rg.invD[A]))
-                                         : (float)B * fabsf(inv[A]);
     const int cn = pos ? c[A] + S : c[A] - S;
     const bool out = cn < 0 || cn >= g.nf[A];
     int nc[3];
@@ -621,43 +652,66 @@ __device__ void march_amr_axis(RTState<NBT> &r, const GridView &g, const double 
     nc[A1] = c[A1];
     nc[A2] = c[A2];
     const int en = out ? 0 : map_entry(g, nc[0], nc[1], nc[2]);
-    const int64_t boff = (int64_t)code << (3 * g.log2B);
+    const int idx = (pos ? 0 : (B - 1) * sA) + ((c[A1] >> shift) & (B - 1)) * sA1 +
+                    ((c[A2] >> shift) & (B - 1)) * sA2;
+    const float ds = a1 * __int_as_float((127 + shift) << 23);  // a1 2^shift
+    const int64_t boff = (int64_t)code << (3 * lb);
     const void *cb = FMT == kCellRho ? (const void *)((const float *)g.cells + boff)
                                      : (const void *)((const uint2 *)g.cells + boff);
-    march_block<NBT, FMT, int, DIR>(r, Q, Dl, inv, tend, lc[0], lc[1], lc[2], B, B, B, B, B * B,
-                                    cb, bc, br);
+    march_column<NBT, FMT, U, int>(r, cb, idx, d, B, ds, bc, br);
     if (out) break;
     c[A] = cn;
     e = en;
   }
 }
 
+// The uniform grid's version: the whole column of nf[A] cells.
+template <int NBT, int FMT, int A, int U>
+__device__ __forceinline__ void march_uniform_axis(RTState<NBT> &r, const GridView &g, const int c[3],
+                                   const RayGeom &rg, const BandCtx &bc, const BandRegs<NBT> &br) {
+  constexpr int A1 = (A + 1) % 3, A2 = (A + 2) % 3;
+  const bool pos = rg.Dhi[A] > 0.f;
+  const int64_t st[3] = {1, (int64_t)g.nf[0], (int64_t)g.nf[0] * g.nf[1]};
+  const int64_t idx = (pos ? 0 : (int64_t)(g.nf[A] - 1) * st[A]) + (int64_t)c[A1] * st[A1] +
+                      (int64_t)c[A2] * st[A2];
+  march_column<NBT, FMT, U, int64_t>(r, g.cells, idx, pos ? st[A] : -st[A], g.nf[A],
+                                     fabsf(rg.invDhi[A]), bc, br);
+}
+
+// Pixel (L, i, j)'s ray along grid axis A through either kind of grid.
+template <int NBT, bool AMR, int FMT, int A, int U>
+__device__ __forceinline__ void march_axis(RTState<NBT> &st, const GridView &g, const RayGeom &rg,
+                                           int L, int i, int j, const BandCtx &bc,
+                                           const BandRegs<NBT> &br) {
+  int c[3];
+  if (!axis_ray_setup<A>(g, rg, L, i, j, c)) return;
+  if (AMR) march_amr_axis<NBT, FMT, A, U>(st, g, c, rg, bc, br);
+  else march_uniform_axis<NBT, FMT, A, U>(st, g, c, rg, bc, br);
+}
+
 // One ray (pixel (L, i, j)) through the grid, bands [b0, b0 + NBT) of bc/br.
+// DIR = 1 + A: every ray of the launch is parallel to grid axis A.
 template <int NBT, bool AMR, int FMT, int DIR = 0>
 __device__ __forceinline__ void trace_ray(RTState<NBT> &st, const GridView &g, const RayGeom &rg,
                                           int L, int i, int j, int fp64_level, const BandCtx &bc,
                                           const BandRegs<NBT> &br) {
   rt_init<NBT>(st);
-  double O[3], t0;
-  int eax;
-  if (ray_setup(g, rg, L, i, j, O, t0, eax)) {
-    if (AMR) {
-      if constexpr (DIR >= 1) {
-        march_amr_axis<NBT, FMT, DIR>(st, g, O, rg, t0, fp64_level, bc, br);
-      } else {
-        // a ray along one grid axis takes the brick walk of the one-axis forms
-        const bool m0 = rg.Dhi[0] != 0.f, m1 = rg.Dhi[1] != 0.f, m2 = rg.Dhi[2] != 0.f;
-        if (m0 + m1 + m2 == 1) {
-          if (m0) march_amr_axis<NBT, FMT, 1>(st, g, O, rg, t0, fp64_level, bc, br);
-          else if (m1) march_amr_axis<NBT, FMT, 2>(st, g, O, rg, t0, fp64_level, bc, br);
-          else march_amr_axis<NBT, FMT, 3>(st, g, O, rg, t0, fp64_level, bc, br);
-        } else {
-          march_amr<NBT, FMT, DIR>(st, g, O, rg, t0, eax, fp64_level, bc, br);
-        }
-      }
-    } else {
-      march_uniform<NBT, FMT, DIR>(st, g, O, rg, t0, bc, br);
+  constexpr int U = ColumnUnroll<DIR>::value;
+  if constexpr (DIR >= 1) {
+    march_axis<NBT, AMR, FMT, (DIR - 1) % 3, U>(st, g, rg, L, i, j, bc, br);
+  } else {
+    const bool m0 = rg.Dhi[0] != 0.f, m1 = rg.Dhi[1] != 0.f, m2 = rg.Dhi[2] != 0.f;
+    if (m0 + m1 + m2 == 1) {
+      if (m0) march_axis<NBT, AMR, FMT, 0, U>(st, g, rg, L, i, j, bc, br);
+      else if (m1) march_axis<NBT, AMR, FMT, 1, U>(st, g, rg, L, i, j, bc, br);
+      else march_axis<NBT, AMR, FMT, 2, U>(st, g, rg, L, i, j, bc, br);
+      return;
     }
+    double O[3], t0;
+    int eax;
+    if (!ray_setup(g, rg, L, i, j, O, t0, eax)) return;
+    if (AMR) march_amr<NBT, FMT>(st, g, O, rg, t0, eax, fp64_level, bc, br);
+    else march_uniform<NBT, FMT>(st, g, O, rg, t0, bc, br);
   }
 }
 

@@ -110,6 +110,18 @@ __device__ __forceinline__ void block_scan_emit(Pred pred, Emit &emit, int64_t n
 // same. Flags of nodes outside the list are kept at zero (a refined node's
 // flag is cleared when its children are emitted, children start at zero).
 
+// Level-map entries of the four children (first index c0, level l) of the
+// level-(l - 1) pixel (i, j); only levels l < Lm have maps.
+__device__ __forceinline__ void set_level_map(int32_t *lmap, int n0, int l, int i, int j,
+                                              int64_t c0) {
+  const int64_t nl = (int64_t)n0 << l;
+  int32_t *row = lmap + level_map_offset(n0, l) + (int64_t)(2 * j) * nl + 2 * i;
+  row[0] = (int32_t)c0;
+  row[1] = (int32_t)(c0 + 1);
+  row[nl] = (int32_t)(c0 + 2);
+  row[nl + 1] = (int32_t)(c0 + 3);
+}
+
 __global__ void k_iota(int32_t *list, int64_t m) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < m) list[i] = (int32_t)i;
@@ -117,19 +129,20 @@ __global__ void k_iota(int32_t *list, int64_t m) {
 
 __global__ void k_xi_scan_list(TreeView t, const int32_t *__restrict__ open, int64_t m,
                                double xi_crit, int xi_norm, int refine_on,
-                               uint32_t *__restrict__ flag) {
+                               uint32_t *__restrict__ flag, const int32_t *lmap) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   const int64_t k = open[i];
-  flag[k] = xi_flag(t, 0, k, xi_crit, xi_norm, refine_on);
+  flag[k] = xi_flag(t, NodeLookup{0, lmap}, k, xi_crit, xi_norm, refine_on);
 }
 
 __global__ void k_balance_list(TreeView t, const int32_t *__restrict__ open, int64_t m,
-                               uint32_t *__restrict__ flag, uint32_t *__restrict__ err) {
+                               uint32_t *__restrict__ flag, uint32_t *__restrict__ err,
+                               const int32_t *lmap) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
     const int k = open[i];
-    if (flag[k] != 0) balance_from(t, 0, k, flag, err);
+    if (flag[k] != 0) balance_from(t, NodeLookup{0, lmap}, k, flag, err);
   }
 }
 
@@ -209,7 +222,7 @@ __global__ void __launch_bounds__(1024) k_scan_blocks3(const int32_t *bcount, in
 __global__ void __launch_bounds__(kScanBlock) k_emit3(TreeView t, const int32_t *open, int64_t m,
                                                       uint32_t *flag, int Lm, const int64_t *boff,
                                                       const int64_t *total, int64_t nb,
-                                                      int64_t n_old, int32_t *next) {
+                                                      int64_t n_old, int32_t *next, int32_t *lmap) {
   __shared__ int32_t wsum[3][kScanBlock / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t start = (int64_t)blockIdx.x * kScanItems;
@@ -256,6 +269,7 @@ __global__ void __launch_bounds__(kScanBlock) k_emit3(TreeView t, const int32_t 
         const int64_t r2 = keep_total + 4 * (run2 + p2 + __popc(b2 & below));
 #pragma unroll
         for (int c = 0; c < 4; ++c) next[r2 + c] = (int32_t)(c0 + c);
+        if (lmap) set_level_map(lmap, t.n0, L, i, j, c0);
       }
     } else if (q.keep) {
       next[run1 + p1 + __popc(b1 & below)] = k;
@@ -264,6 +278,205 @@ __global__ void __launch_bounds__(kScanBlock) k_emit3(TreeView t, const int32_t 
     run1 += t1;
     run2 += t2;
     __syncthreads();
+  }
+}
+
+// ---- the sweep with counts on the device ----------------------------------
+// The same steps as above over open[S->cur] with m = S->m items; grids are a
+// few blocks per SM and loop over the items (k_count3d and k_emit3d over scan
+// chunks of kScanItems, chunk c's counts at bcount[sel * nb_cap + c]).
+
+__global__ void k_xi_scan_dev(TreeView t, const int32_t *__restrict__ open0,
+                              const int32_t *__restrict__ open1, const SweepState *__restrict__ S,
+                              double xi_crit, int xi_norm, int refine_on,
+                              uint32_t *__restrict__ flag, const int32_t *lmap) {
+  wait_prior_grid();
+  if (S->done) return;
+  const int64_t m = S->m;
+  const int32_t *open = S->cur ? open1 : open0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    const int64_t k = open[i];
+    flag[k] = xi_flag(t, NodeLookup{0, lmap}, k, xi_crit, xi_norm, refine_on);
+  }
+}
+
+// Scan and balance in one pass (counts on the device). Flags of the open
+// list are all zero when a sweep starts (a refined node's flag is cleared
+// with its children's, new children start at zero), so a thread only ever
+// sets flags: a leaf whose xi reaches xi_crit is flagged, and the thread that
+// moves a flag from 0 to 1 -- the scan's or a balance expansion's -- expands
+// it. Every flag is expanded once, and the flags reach the same closure as a
+// scan of every leaf followed by the balance.
+__global__ void k_scan_balance_dev(TreeView t, const int32_t *__restrict__ open0,
+                                   const int32_t *__restrict__ open1,
+                                   const SweepState *__restrict__ S, double xi_crit, int xi_norm,
+                                   int refine_on, uint32_t *__restrict__ flag,
+                                   uint32_t *__restrict__ err, const int32_t *lmap) {
+  wait_prior_grid();
+  if (S->done) return;
+  const int64_t m = S->m;
+  const int32_t *open = S->cur ? open1 : open0;
+  const NodeLookup look{0, lmap};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    const int k = open[i];
+    if (xi_flag(t, look, k, xi_crit, xi_norm, refine_on) && atomicExch(flag + k, 1u) == 0u)
+      balance_from(t, look, k, flag, err);
+  }
+}
+
+__global__ void k_balance_dev(TreeView t, const int32_t *__restrict__ open0,
+                              const int32_t *__restrict__ open1, const SweepState *__restrict__ S,
+                              uint32_t *__restrict__ flag, uint32_t *__restrict__ err,
+                              const int32_t *lmap) {
+  wait_prior_grid();
+  if (S->done) return;
+  const int64_t m = S->m;
+  const int32_t *open = S->cur ? open1 : open0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    const int k = open[i];
+    if (flag[k] != 0) balance_from(t, NodeLookup{0, lmap}, k, flag, err);
+  }
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_count3d(TreeView t, const int32_t *open0,
+                                                        const int32_t *open1,
+                                                        const SweepState *__restrict__ S,
+                                                        const uint32_t *flag, int32_t *bcount,
+                                                        int64_t nb_cap) {
+  wait_prior_grid();
+  if (S->done) return;
+  __shared__ int32_t wsum[3][kScanBlock / 32];
+  const int64_t m = S->m;
+  const int32_t *open = S->cur ? open1 : open0;
+  const int64_t nb = scan_chunks(m);
+  for (int64_t c = blockIdx.x; c < nb; c += gridDim.x) {
+    const int64_t start = c * kScanItems;
+    int32_t c0 = 0, c1 = 0, c2 = 0;
+    for (int rr = 0; rr < kScanRounds; ++rr) {
+      int k;
+      const ListSel q = list_sel(t, open, m, flag, t.Lm, start + (int64_t)rr * kScanBlock + threadIdx.x, k);
+      c0 += __popc(__ballot_sync(0xffffffffu, q.f));
+      c1 += __popc(__ballot_sync(0xffffffffu, q.keep));
+      c2 += __popc(__ballot_sync(0xffffffffu, q.co));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      wsum[0][threadIdx.x >> 5] = c0;
+      wsum[1][threadIdx.x >> 5] = c1;
+      wsum[2][threadIdx.x >> 5] = c2;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      int32_t sum = 0;
+      for (int w = 0; w < kScanBlock / 32; ++w) sum += wsum[threadIdx.x][w];
+      bcount[threadIdx.x * nb_cap + c] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+// Block b scans selection b's chunk counts; totals to S->tot, and block 0
+// sets S->done when nothing was flagged (blocks 1 and 2 may then see it and
+// return early: their totals are not needed once the loop has ended).
+__global__ void __launch_bounds__(1024) k_scan_blocks3d(const int32_t *bcount, int64_t nb_cap,
+                                                        int64_t *boff, SweepState *S) {
+  wait_prior_grid();
+  if (S->done) return;
+  __shared__ int64_t part[1024];
+  const int64_t nb = scan_chunks(S->m);
+  const int32_t *bc = bcount + blockIdx.x * nb_cap;
+  int64_t *bo = boff + blockIdx.x * nb_cap;
+  const int64_t per = (nb + 1023) / 1024;
+  const int64_t a = threadIdx.x * per, b = min(nb, a + per);
+  int64_t s = 0;
+  for (int64_t x = a; x < b; ++x) s += bc[x];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const int64_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int64_t run = part[threadIdx.x] - s;
+  for (int64_t x = a; x < b; ++x) {
+    bo[x] = run;
+    run += bc[x];
+  }
+  if (threadIdx.x == 1023) {
+    S->tot[blockIdx.x] = part[1023];
+    if (blockIdx.x == 0 && part[1023] == 0) S->done = 1;  // nothing flagged: the loop ends
+  }
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_emit3d(TreeView t, int32_t *open0,
+                                                       int32_t *open1, const SweepState *__restrict__ S,
+                                                       uint32_t *flag, const int64_t *boff,
+                                                       int64_t nb_cap, int32_t *lmap) {
+  wait_prior_grid();
+  if (S->done) return;
+  __shared__ int32_t wsum[3][kScanBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t m = S->m, n_old = S->n, keep_total = S->tot[1];
+  const int32_t *open = S->cur ? open1 : open0;
+  int32_t *next = S->cur ? open0 : open1;
+  const int64_t nb = scan_chunks(m);
+  const uint32_t below = (1u << lane) - 1u;
+  for (int64_t c = blockIdx.x; c < nb; c += gridDim.x) {
+    const int64_t start = c * kScanItems;
+    int64_t run0 = boff[c], run1 = boff[nb_cap + c], run2 = boff[2 * nb_cap + c];
+    for (int rr = 0; rr < kScanRounds; ++rr) {
+      int k;
+      const ListSel q = list_sel(t, open, m, flag, t.Lm, start + (int64_t)rr * kScanBlock + threadIdx.x, k);
+      const uint32_t b0 = __ballot_sync(0xffffffffu, q.f);
+      const uint32_t b1 = __ballot_sync(0xffffffffu, q.keep);
+      const uint32_t b2 = __ballot_sync(0xffffffffu, q.co);
+      if (lane == 0) {
+        wsum[0][warp] = __popc(b0);
+        wsum[1][warp] = __popc(b1);
+        wsum[2][warp] = __popc(b2);
+      }
+      __syncthreads();
+      int32_t p0 = 0, p1 = 0, p2 = 0, t0 = 0, t1 = 0, t2 = 0;
+#pragma unroll
+      for (int w = 0; w < kScanBlock / 32; ++w) {
+        const int32_t v0 = wsum[0][w], v1 = wsum[1][w], v2 = wsum[2][w];
+        p0 += w < warp ? v0 : 0;
+        p1 += w < warp ? v1 : 0;
+        p2 += w < warp ? v2 : 0;
+        t0 += v0;
+        t1 += v1;
+        t2 += v2;
+      }
+      if (q.f) {
+        const int64_t c0 = n_old + 4 * (run0 + p0 + __popc(b0 & below));
+        const int L = t.lvl[k] + 1, i = t.pi[k], j = t.pj[k];
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+          t.lvl[c0 + ch] = (int8_t)L;
+          t.pi[c0 + ch] = 2 * i + (ch & 1);
+          t.pj[c0 + ch] = 2 * j + (ch >> 1);
+          t.child[c0 + ch] = -1;
+          flag[c0 + ch] = 0u;
+        }
+        t.child[k] = (int32_t)c0;
+        flag[k] = 0u;
+        if (q.co) {
+          const int64_t r2 = keep_total + 4 * (run2 + p2 + __popc(b2 & below));
+#pragma unroll
+          for (int ch = 0; ch < 4; ++ch) next[r2 + ch] = (int32_t)(c0 + ch);
+          if (lmap) set_level_map(lmap, t.n0, L, i, j, c0);
+        }
+      } else if (q.keep) {
+        next[run1 + p1 + __popc(b1 & below)] = k;
+      }
+      run0 += t0;
+      run1 += t1;
+      run2 += t2;
+      __syncthreads();
+    }
   }
 }
 
@@ -396,7 +609,7 @@ static unsigned stride_blocks(int64_t n, int block, int per_sm) {
   return (unsigned)(need < cap ? need : cap);
 }
 
-int64_t scan_blocks(int64_t n) { return (n + kScanItems - 1) / kScanItems; }
+int64_t scan_blocks(int64_t n) { return scan_chunks(n); }
 
 cudaError_t launch_list_init(int32_t *list, int64_t m, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
@@ -405,16 +618,17 @@ cudaError_t launch_list_init(int32_t *list, int64_t m, cudaStream_t st) {
 }
 
 cudaError_t launch_list_scan(const TreeView &t, const int32_t *open, int64_t m, double xi_crit,
-                             int xi_norm, int refine_on, uint32_t *flag, cudaStream_t st) {
+                             int xi_norm, int refine_on, uint32_t *flag, cudaStream_t st,
+                             const int32_t *lmap) {
   if (m <= 0) return cudaSuccess;
-  k_xi_scan_list<<<nblk(m, 256), 256, 0, st>>>(t, open, m, xi_crit, xi_norm, refine_on, flag);
+  k_xi_scan_list<<<nblk(m, 256), 256, 0, st>>>(t, open, m, xi_crit, xi_norm, refine_on, flag, lmap);
   return cudaGetLastError();
 }
 
 cudaError_t launch_list_balance(const TreeView &t, const int32_t *open, int64_t m, uint32_t *flag,
-                                uint32_t *err, cudaStream_t st) {
+                                uint32_t *err, cudaStream_t st, const int32_t *lmap) {
   if (m <= 0) return cudaSuccess;
-  k_balance_list<<<stride_blocks(m, 128, 16), 128, 0, st>>>(t, open, m, flag, err);
+  k_balance_list<<<stride_blocks(m, 128, 16), 128, 0, st>>>(t, open, m, flag, err, lmap);
   return cudaGetLastError();
 }
 
@@ -430,10 +644,10 @@ cudaError_t launch_list_count(const TreeView &t, const int32_t *open, int64_t m,
 
 cudaError_t launch_list_emit(const TreeView &t, const int32_t *open, int64_t m, uint32_t *flag,
                              const int64_t *boff, const int64_t *totals, int64_t n_old,
-                             int32_t *next, cudaStream_t st) {
+                             int32_t *next, cudaStream_t st, int32_t *lmap) {
   const int64_t nb = scan_blocks(m);
   if (nb == 0) return cudaSuccess;
-  k_emit3<<<(unsigned)nb, kScanBlock, 0, st>>>(t, open, m, flag, t.Lm, boff, totals, nb, n_old, next);
+  k_emit3<<<(unsigned)nb, kScanBlock, 0, st>>>(t, open, m, flag, t.Lm, boff, totals, nb, n_old, next, lmap);
   return cudaGetLastError();
 }
 
@@ -470,6 +684,52 @@ cudaError_t launch_emit_out(const TreeView &t, const OutView &o, int all, int64_
   k_emit_out<<<(unsigned)nb, kScanBlock, 0, st>>>(t, o, all, n, boff);
   return cudaGetLastError();
 }
+
+// Blocks of the device-count sweep kernels: a few per SM, looping over items.
+static unsigned sweep_blocks(int per_sm) { return (unsigned)(sm_count() * per_sm); }
+
+cudaError_t launch_sweep_scan(const TreeView &t, int32_t *const open[2], const SweepState *S,
+                              double xi_crit, int xi_norm, int refine_on, uint32_t *flag,
+                              cudaStream_t st, const int32_t *lmap) {
+  return launch_pdl(k_xi_scan_dev, dim3(sweep_blocks(8)), dim3(256), 0, st, t,
+                    (const int32_t *)open[0], (const int32_t *)open[1], S, xi_crit, xi_norm,
+                    refine_on, flag, lmap);
+}
+
+cudaError_t launch_sweep_scan_balance(const TreeView &t, int32_t *const open[2],
+                                      const SweepState *S, double xi_crit, int xi_norm,
+                                      int refine_on, uint32_t *flag, uint32_t *err,
+                                      cudaStream_t st, const int32_t *lmap) {
+  return launch_pdl(k_scan_balance_dev, dim3(sweep_blocks(8)), dim3(256), 0, st, t,
+                    (const int32_t *)open[0], (const int32_t *)open[1], S, xi_crit, xi_norm,
+                    refine_on, flag, err, lmap);
+}
+
+cudaError_t launch_sweep_balance(const TreeView &t, int32_t *const open[2], const SweepState *S,
+                                 uint32_t *flag, uint32_t *err, cudaStream_t st,
+                                 const int32_t *lmap) {
+  return launch_pdl(k_balance_dev, dim3(sweep_blocks(16)), dim3(128), 0, st, t,
+                    (const int32_t *)open[0], (const int32_t *)open[1], S, flag, err, lmap);
+}
+
+cudaError_t launch_sweep_count(const TreeView &t, int32_t *const open[2], SweepState *S,
+                               const uint32_t *flag, int32_t *bcount, int64_t *boff,
+                               int64_t nb_cap, cudaStream_t st) {
+  cudaError_t e = launch_pdl(k_count3d, dim3(sweep_blocks(8)), dim3(kScanBlock), 0, st, t,
+                             (const int32_t *)open[0], (const int32_t *)open[1],
+                             (const SweepState *)S, flag, bcount, nb_cap);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(k_scan_blocks3d, dim3(3), dim3(1024), 0, st, (const int32_t *)bcount, nb_cap,
+                    boff, S);
+}
+
+cudaError_t launch_sweep_emit(const TreeView &t, int32_t *const open[2], const SweepState *S,
+                              uint32_t *flag, const int64_t *boff, int64_t nb_cap,
+                              cudaStream_t st, int32_t *lmap) {
+  return launch_pdl(k_emit3d, dim3(sweep_blocks(8)), dim3(kScanBlock), 0, st, t, open[0], open[1],
+                    S, flag, boff, nb_cap, lmap);
+}
+
 
 int64_t flux_blocks(int64_t n) {
   const int64_t per = 8192;

@@ -19,6 +19,33 @@ __device__ __forceinline__ int descend(const TreeView &t, int base0, int L, int 
   return k;
 }
 
+// Level maps of a single-view tree: for every level 1 <= l < Lm a dense
+// (n0 2^l)^2 array of node indices (-1 where no node exists), written when
+// the node is created; level 0 is implicit (node j n0 + i). The deepest node
+// at a level <= L covering level-L pixel (i, j) is then found by at most L
+// independent loads (one, or two next to a coarser neighbour, in a balanced
+// tree) instead of a chain of L dependent child-link hops.
+__device__ __forceinline__ int map_deepest(const TreeView &t, const int32_t *__restrict__ lmap, int L,
+                                           int i, int j) {
+  for (int l = L; l >= 1; --l) {
+    const int s = L - l;
+    const int64_t nl = (int64_t)t.n0 << l;
+    const int q = __ldg(lmap + level_map_offset(t.n0, l) + (int64_t)(j >> s) * nl + (i >> s));
+    if (q >= 0) return q;
+  }
+  return (j >> L) * t.n0 + (i >> L);
+}
+
+// The deepest node at a level <= L covering level-L pixel (i, j): through the
+// level maps when the tree has them, else by descent from the base pixel.
+struct NodeLookup {
+  int base0;              // index of the view's base pixel (0, 0)
+  const int32_t *lmap;   // level maps (single view, base0 = 0), or NULL
+  __device__ __forceinline__ int operator()(const TreeView &t, int L, int i, int j) const {
+    return lmap ? map_deepest(t, lmap, L, i, j) : descend(t, base0, L, i, j);
+  }
+};
+
 // Numerator and denominator of Eq. 2 (squared) on the 3x3 stencil
 // s[3*(dj+1) + (di+1)], FP64 with every operation rounded separately (no
 // fused multiply-add), in a fixed order.
@@ -68,8 +95,58 @@ __device__ __forceinline__ bool xi_at_least(const double s[9], int xi_norm, doub
   return (x > 1.0 ? 1.0 : x) >= xi_crit;
 }
 
+// xi_at_least decided in FP32 where the answer is clear: 1 (xi >= xi_crit),
+// 0 (xi < xi_crit) or -1 (too close to call: take the FP64 path). FP64 runs
+// at a small fraction of the FP32 rate on this GPU, and most stencils are far
+// from the threshold.
+//
+// With A = max |f_m| and u = 2^-24, each FP32 operation of the numerator and
+// denominator below rounds with relative error <= u, and a first-order count
+// over the operations (second differences <= 4A, first differences <= 2A,
+// squares <= 16A^2, sums <= 34A^2) bounds |num32 - num| <= 221 u A^2 and
+// |den32 - den| <= 192 u A^2 (twice that with xi_norm = 1); E = 512 u A^2 is
+// used for both. The answer is 1 when num32 - E > (den32 + E) xi_crit^2
+// (1 + 2^-9) and 0 when num32 + E < (den32 - E) xi_crit^2 (1 - 2^-9): then the
+// exact num and den satisfy the strict inequality with margin 2^-11, which
+// exceeds the FP64 path's rounding (about 2^-44 A^2 absolute, against num or
+// den of at least E xi_crit^2 >= 2^-23 A^2 when xi_crit >= 1/16) by orders of
+// magnitude, so the FP64 path returns the same. Outside 1/16 <= xi_crit <= 1
+// the answer is -1 (the FP64 path's own rules for xi_crit <= 0 and > 1 then
+// apply); A = 0 (all nine values zero) is 0, as the FP64 path's num == 0 rule
+// gives; with A outside [2^-50, 2^60] (squares and bounds must stay normal
+// FP32 numbers) the answer is -1.
+__device__ __forceinline__ int xi_at_least_f32(const float f[9], int xi_norm, double xi_crit) {
+  if (!(xi_crit >= 0.0625 && xi_crit <= 1.0)) return -1;
+  float A = 0.f;
+#pragma unroll
+  for (int m = 0; m < 9; ++m) A = fmaxf(A, fabsf(f[m]));
+  if (A == 0.f) return 0;
+  if (!(A >= 0x1p-50f && A <= 0x1p60f)) return -1;
+  const float c = f[4], xm = f[3], xp = f[5], ym = f[1], yp = f[7];
+  const float mm = f[0], pm = f[2], mp = f[6], pp = f[8];
+  const float c2 = 2.f * c;
+  const float d2u = __fadd_rn(__fsub_rn(xp, c2), xm);
+  const float d2v = __fadd_rn(__fsub_rn(yp, c2), ym);
+  const float duv = __fmul_rn(__fadd_rn(__fsub_rn(__fsub_rn(pp, pm), mp), mm), 0.25f);
+  const float num = __fadd_rn(__fadd_rn(__fmul_rn(d2u, d2u), __fmul_rn(d2v, d2v)),
+                              __fmul_rn(2.f, __fmul_rn(duv, duv)));
+  const float au = __fadd_rn(fabsf(__fsub_rn(xp, c)), fabsf(__fsub_rn(c, xm)));
+  const float av = __fadd_rn(fabsf(__fsub_rn(yp, c)), fabsf(__fsub_rn(c, ym)));
+  float den = __fadd_rn(__fmul_rn(au, au), __fmul_rn(av, av));
+  float E = __fmul_rn(0x1p-15f, __fmul_rn(A, A));  // 512 u A^2
+  if (xi_norm == 1) {
+    den = 2.f * den;
+  }
+  const float Ed = xi_norm == 1 ? 2.f * E : E;
+  const float x2 = (float)(xi_crit * xi_crit);
+  const float c_hi = x2 * (1.f + 0x1p-9f), c_lo = x2 * (1.f - 0x1p-9f);
+  if (__fsub_rn(num, E) > __fmul_rn(__fadd_rn(den, Ed), c_hi)) return 1;
+  if (__fadd_rn(num, E) < __fmul_rn(__fsub_rn(den, Ed), c_lo)) return 0;
+  return -1;
+}
+
 // Step iii for node k: 1 if it is a leaf below max_level with xi >= xi_crit.
-__device__ __forceinline__ uint32_t xi_flag(const TreeView &t, int base0, int64_t k,
+__device__ __forceinline__ uint32_t xi_flag(const TreeView &t, NodeLookup look, int64_t k,
                                             double xi_crit, int xi_norm, int refine_on) {
   const int L = t.lvl[k];
   if (t.child[k] >= 0 || L >= t.Lm) return 0u;
@@ -81,19 +158,32 @@ __device__ __forceinline__ uint32_t xi_flag(const TreeView &t, int base0, int64_
 #pragma unroll
     for (int di = -1; di <= 1; ++di) {
       const int ii = min(max(i + di, 0), nl - 1), jj = min(max(j + dj, 0), nl - 1);
-      q[3 * (dj + 1) + (di + 1)] = (di == 0 && dj == 0) ? (int)k : descend(t, base0, L, ii, jj);
+      q[3 * (dj + 1) + (di + 1)] = (di == 0 && dj == 0) ? (int)k : look(t, L, ii, jj);
     }
   uint32_t f = 0;
+  float v[9];
   double s[9];
   if (refine_on == 0 || refine_on == 2) {
 #pragma unroll
-    for (int m = 0; m < 9; ++m) s[m] = (double)t.p[q[m]];
-    f |= xi_at_least(s, xi_norm, xi_crit);
-  }
-  if (refine_on == 1 || refine_on == 2) {
+    for (int m = 0; m < 9; ++m) v[m] = t.p[q[m]];
+    int d = xi_at_least_f32(v, xi_norm, xi_crit);
+    if (d < 0) {
 #pragma unroll
-    for (int m = 0; m < 9; ++m) s[m] = (double)t.N[q[m]];
-    f |= xi_at_least(s, xi_norm, xi_crit);
+      for (int m = 0; m < 9; ++m) s[m] = (double)v[m];
+      d = xi_at_least(s, xi_norm, xi_crit);
+    }
+    f |= (uint32_t)d;
+  }
+  if (f == 0 && (refine_on == 1 || refine_on == 2)) {
+#pragma unroll
+    for (int m = 0; m < 9; ++m) v[m] = t.N[q[m]];
+    int d = xi_at_least_f32(v, xi_norm, xi_crit);
+    if (d < 0) {
+#pragma unroll
+      for (int m = 0; m < 9; ++m) s[m] = (double)v[m];
+      d = xi_at_least(s, xi_norm, xi_crit);
+    }
+    f |= (uint32_t)d;
   }
   return f;
 }
@@ -101,7 +191,7 @@ __device__ __forceinline__ uint32_t xi_flag(const TreeView &t, int base0, int64_
 // Step iii, balance: a flagged leaf at level L forces every leaf at a level
 // < L that covers one of its 8 same-level neighbours, and so on down the
 // levels. Each newly set flag is expanded by the thread that set it.
-__device__ __forceinline__ void balance_from(const TreeView &t, int base0, int k0,
+__device__ __forceinline__ void balance_from(const TreeView &t, NodeLookup look, int k0,
                                              uint32_t *__restrict__ flag,
                                              uint32_t *__restrict__ err) {
   int stack[kBalanceStack];
@@ -116,7 +206,7 @@ __device__ __forceinline__ void balance_from(const TreeView &t, int base0, int k
         if (!di && !dj) continue;
         const int ii = i + di, jj = j + dj;
         if (ii < 0 || jj < 0 || ii >= nl || jj >= nl) continue;
-        const int m = descend(t, base0, L, ii, jj);
+        const int m = look(t, L, ii, jj);
         if (t.child[m] < 0 && t.lvl[m] < L) {
           if (atomicExch(flag + m, 1u) == 0u) {
             if (sp < kBalanceStack) stack[sp++] = m;

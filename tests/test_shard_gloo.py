@@ -100,3 +100,55 @@ def test_failing_rank_is_reported():
     assert out[1][1] == "error" and "injected" in out[1][2]
     # the healthy rank either finished its gather or reports the broken group
     assert out[0][1] == "error" or isinstance(out[0][1], list)
+
+
+# ---- one image, rays of every sweep split over ranks --------------------------
+def _slice_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        out = []
+        for count in (0, 1, 2, 5, 17, 1000):
+            full_f = torch.arange(count, dtype=torch.float32) * 1.5 + 0.25
+            full_i = torch.arange(count, dtype=torch.int32) * 7 - 3
+            f = torch.full((count,), float("nan"))
+            i = torch.full((count,), -99, dtype=torch.int32)
+            lo, hi = shard.ray_slices(count, world)[rank]
+            f[lo:hi] = full_f[lo:hi]
+            i[lo:hi] = full_i[lo:hi]
+            shard.exchange_slices([f, i], rank, world)
+            out.append(bool(torch.equal(f, full_f)) and bool(torch.equal(i, full_i)))
+        q.put((rank, out))
+    except Exception as e:
+        q.put((rank, "error: " + str(e)))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_ray_slice_exchange(world):
+    """exchange_slices (the host side of air_render_adaptive_sharded) fills
+    every rank's arrays with every slice, for counts below, at and above the
+    number of ranks."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_slice_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in ps:
+        p.start()
+    res = [q.get(timeout=120) for _ in range(world)]
+    for p in ps:
+        p.join(timeout=60)
+    for rank, out in res:
+        assert out == [True] * 6, (rank, out)
+
+
+def test_ray_slices_cover_each_ray_once():
+    for count in (0, 1, 3, 10, 1001):
+        for world in (1, 2, 3, 8):
+            sl = shard.ray_slices(count, world)
+            assert sl[0][0] == 0 and sl[-1][1] == count
+            assert all(a[1] == b[0] for a, b in zip(sl, sl[1:]))
+            assert max(h - l for l, h in sl) - min(h - l for l, h in sl) <= 1
