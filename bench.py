@@ -134,7 +134,7 @@ def oracle_sample_rate(sc, view, n0, budget_s=15.0, chunk=65536, max_rays=1 << 2
     return steps / t_used, done, t_used
 
 
-MARCH_SOURCES = ("air_march.cuh", "air_march.cu", "air_internal.cuh")
+MARCH_SOURCES = ("air_march.cuh", "air_march.cu", "air_internal.cuh", "air_refine.cuh")
 
 
 def march_source_hash():
@@ -249,11 +249,68 @@ def run_batch(args):
     ms_seq, s1 = _timed(seq, st)
     best = min(res.values(), key=lambda r: r["ms"])
     same = all(b["n_rays"] == a["n_rays"] and b["n_steps"] == a["n_steps"] for a, b in zip(s1, b))
+    # batched with the learned proposal: a network trained on plain trees of
+    # 16 other views of this grid (outside the timed region)
+    lrn = learned_batch_record(air, torch, g, vs, W["base_res"], W["max_level"], W["xi_crit"], st,
+                               train_views=scenes.random_views(4, 16), plain=b, plain_ms=best["ms"],
+                               quantiles=(0.3, 0.5, 0.8))
+    # fixed 4096^2 images of two of the views
+    g.render_fixed(vs[0], 512, fields=("band_flux",))
+    fx = [_timed(lambda: g.render_fixed(v, W["fixed_res"], fields=("band_flux",)), st) for v in vs[:2]]
+    fixed_view_ms = float(np.mean([x[0] for x in fx]))
+    ferr = [abs(float(s1[k]["band_flux"].double().sum()) - float(fx[k][1]["band_flux"].double().sum())) /
+            abs(float(fx[k][1]["band_flux"].double().sum())) for k in range(2)]
     print(json.dumps({"workload": "batch: cone grid, 64 random views x 16 bands, base 256^2, "
                                   "max level 4, xi_crit 0.5", "rays": sum(r["n_rays"] for r in b),
                       "steps": best["steps"], "batch": res, "sequential_ms": ms_seq,
                       "batch_speedup_vs_sequential": ms_seq / best["ms"],
-                      "per_view_rays_and_steps_equal_to_sequential": same}), flush=True)
+                      "per_view_rays_and_steps_equal_to_sequential": same,
+                      "batched_learned": lrn, "fixed_per_view_ms": fixed_view_ms,
+                      "fixed_64_views_ms_extrapolated": fixed_view_ms * len(vs),
+                      "batch_speedup_vs_fixed": fixed_view_ms * len(vs) / best["ms"],
+                      "batched_learned_speedup_vs_fixed": fixed_view_ms * len(vs) / lrn["ms"],
+                      "flux_rel_err_vs_fixed_views_0_1": ferr}), flush=True)
+
+
+def learned_batch_record(air, torch, g, vs, n0, Lm, xc, st, train_views, plain, plain_ms,
+                         quantiles=(0.8,)):
+    """Train the depth network on plain trees of `train_views` of grid g (outside
+    any timed region), then time air_render_batch_learned on `vs` at each
+    proposal quantile and check its images against the plain batched render
+    `plain`; the fastest quantile is the record's `ms`."""
+    t0 = time.perf_counter()
+    xs, ys = [], []
+    for v in train_views:
+        x, y = g.learn_samples(v, n0, Lm, xc)
+        xs.append(x)
+        ys.append(y)
+    X, Y = torch.cat(xs), torch.cat(ys)
+    net = air.MLP(scenes.mlp_init(0, scale=1.0))
+    net.train(X, Y, batch=8192, epochs=4, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del X, Y, xs, ys
+    per_q = {}
+    for quantile in quantiles:
+        g.render_batch_learned(vs, n0, Lm, xc, net, quantile=quantile, fields=("band_flux",))
+        ms, (rl, stats) = _timed(lambda: g.render_batch_learned(vs, n0, Lm, xc, net, quantile=quantile,
+                                                                fields=("band_flux",)), st)
+        # band fluxes of batched renders are FP64 atomic sums: equal up to summation order
+        same = all(a["n_rays"] == b["n_rays"] and a["n_steps"] == b["n_steps"] and
+                   np.allclose(a["band_flux"].cpu().numpy(), b["band_flux"].cpu().numpy(), rtol=1e-12,
+                               atol=0) for a, b in zip(rl, plain))
+        per_q[quantile] = dict(ms=ms, speedup_vs_plain_batched=plain_ms / ms,
+                               identical_to_plain_batched=same,
+                               proposed_rays=int(stats["proposed_rays"]), used_rays=int(stats["used_rays"]),
+                               wasted_rays=int(stats["wasted_rays"]),
+                               fallback_rays=int(stats["fallback_rays"]))
+    net.close()
+    best_q = min(per_q, key=lambda q: per_q[q]["ms"])
+    return dict(ms=per_q[best_q]["ms"], quantile=best_q, per_quantile={str(k): v for k, v in per_q.items()},
+                speedup_vs_plain_batched=plain_ms / per_q[best_q]["ms"],
+                identical_to_plain_batched=all(v["identical_to_plain_batched"] for v in per_q.values()),
+                training=f"{len(train_views)} plain trees of other views of the grid, 4 epochs",
+                training_s=train_s)
 
 
 def run_ring(args):
@@ -470,6 +527,22 @@ def run_large(args):
                                         speedup_vs_sequential=ms_seq / ms_l, first_two_identical=same)
     out["learned"] = learned
     del X, Y
+    # batched with the learned proposal (the same network), per quantile
+    bl = {}
+    for qq in (0.3, 0.5, 0.8):
+        g.render_batch_learned(vs, n0, Lm, xc, net, quantile=qq, fields=("band_flux",))
+        ms_q, (rbl, sbl) = _timed(lambda: g.render_batch_learned(vs, n0, Lm, xc, net, quantile=qq,
+                                                                 fields=("band_flux",)), st)
+        bl[str(qq)] = dict(
+            ms=ms_q, speedup_vs_plain_batched=best["ms"] / ms_q,
+            identical_to_plain_batched=all(a["n_rays"] == c["n_rays"] and a["n_steps"] == c["n_steps"] and
+                                           np.allclose(a["band_flux"].cpu().numpy(),
+                                                       c["band_flux"].cpu().numpy(), rtol=1e-12, atol=0)
+                                           for a, c in zip(rbl, b)),
+            **{k: int(v) for k, v in sbl.items() if k in ("proposed_rays", "used_rays", "wasted_rays",
+                                                         "fallback_rays")})
+    out["batched_learned"] = bl
+    ms_bl = min(x["ms"] for x in bl.values())
     # fixed 8192^2 (two views timed)
     g.render_fixed(vs[0], 1024, fields=("band_flux",))
     fx = []
@@ -480,6 +553,7 @@ def run_large(args):
     out["fixed_per_view_ms"] = fixed_view_ms
     out["fixed_16_views_ms_extrapolated"] = fixed_view_ms * W["views"]
     out["batch_speedup_vs_fixed"] = fixed_view_ms * W["views"] / best["ms"]
+    out["batched_learned_speedup_vs_fixed"] = fixed_view_ms * W["views"] / ms_bl
     for k in range(2):
         fs = g.render_fixed(vs[k], W["fixed_res"], fields=("band_flux",))
         fa = fs["band_flux"].double().sum().item()
@@ -534,6 +608,9 @@ def large_view_record(air, torch, st, reps=2):
     g.render_batch([v], n0, Lm, xc, fields=fields)
     batch_ms, rb = timed(lambda: g.render_batch([v], n0, Lm, xc, fields=fields))
     rb = rb[0]
+    lrn = learned_batch_record(air, torch, g, [v], n0, Lm, xc, st,
+                               train_views=scenes.random_views(22, 4), plain=[rb], plain_ms=batch_ms,
+                               quantiles=(0.3, 0.5, 0.8))
     g.render_fixed(v, 1024, fields=fields)
     fixed_ms, rf = timed(lambda: g.render_fixed(v, W["fixed_res"], fields=fields))
     fa = rf["band_flux"].double().cpu().numpy()
@@ -552,6 +629,8 @@ def large_view_record(air, torch, st, reps=2):
                air_sweeps=int(ra["n_sweeps"]),
                batched_ms=batch_ms, batched_equal=bool(rb["n_rays"] == ra["n_rays"] and
                                                       rb["n_steps"] == ra["n_steps"]),
+               batched_learned=lrn,
+               batched_learned_speedup_vs_fixed=fixed_ms / lrn["ms"],
                fixed_ms=fixed_ms, fixed_steps=int(rf["n_steps"]),
                air_speedup_vs_fixed=fixed_ms / air_ms,
                batched_speedup_vs_fixed=fixed_ms / batch_ms,

@@ -289,6 +289,23 @@ AIR_API air_status air_render_learned(air_grid *g, const air_view *view, const a
                                       air_mlp *mlp, const air_learned_opts *opts, air_image *out,
                                       air_learned_stats *stats);
 
+/* Batched adaptive images with the learned proposal: air_render_batch with
+ * the proposal of air_render_learned for every view. The base images of all
+ * views are traced by the persistent kernel; the network proposes a depth for
+ * every base pixel of every view; a second persistent launch traces every
+ * view's proposal wave from one work queue and then runs the sweeps of every
+ * view, taking a new pixel's values from its view's wave where the wave
+ * traced it and tracing the pixels the proposal missed. outs[v] is bitwise
+ * the image air_render_batch (and air_render_adaptive) gives; stats (may be
+ * NULL) sums over the views: proposed_rays, used_rays, wasted_rays,
+ * fallback_rays, sweeps = the most of any view, waves = 2 launches. No CUDA
+ * graph is used (opts->use_graph is ignored). Errors: as air_render_batch and
+ * air_render_learned. */
+AIR_API air_status air_render_batch_learned(air_grid *g, const air_view *views, int32_t n_views,
+                                            const air_params *params, const air_batch_opts *opts,
+                                            air_mlp *mlp, const air_learned_opts *lopts,
+                                            air_image *outs, air_learned_stats *stats);
+
 /* Autotuner (not in the paper): time candidate launch configurations on this
  * grid with this view and parameters (fixed image of up to 2048^2 pixels,
  * adaptive image, and, if n_views_batch > 0, a batch of that many copies of the

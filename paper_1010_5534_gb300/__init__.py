@@ -40,6 +40,7 @@ EXPORTED = ["air_load_grid", "air_set_stream", "air_render_fixed", "air_render_a
             "air_get_tuning",
             "air_profile_enable", "air_profile_read", "air_band_flux_static", "air_render_raster",
             "air_render_adaptive_spectra", "air_render_adaptive_sharded",
+            "air_render_batch_learned",
             "air_free",
             "air_last_error", "air_version"]
 PHASES = ("march", "scan", "balance", "refine", "output", "batch", "learn")
@@ -222,6 +223,11 @@ def lib():
             L.air_band_flux_static.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
                                                C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
                                                C.c_void_p]
+            L.air_render_batch_learned.restype = C.c_int
+            L.air_render_batch_learned.argtypes = [C.c_void_p, C.POINTER(View), C.c_int32,
+                                                   C.POINTER(Params), C.POINTER(BatchOpts),
+                                                   C.c_void_p, C.POINTER(LearnedOpts),
+                                                   C.POINTER(Image), C.POINTER(LearnedStats)]
             L.air_render_adaptive_sharded.restype = C.c_int
             L.air_render_adaptive_sharded.argtypes = [C.c_void_p, C.POINTER(View), C.POINTER(Params),
                                                       C.POINTER(Shard), C.POINTER(Image)]
@@ -446,6 +452,31 @@ class Grid:
         self._batch_hint = {k: int(im.n_out) for k, im in enumerate(ims)}
         return [self._result(im, out) for im, out in zip(ims, outs)]
 
+    def render_batch_learned(self, views, base_res, max_level, xi_crit, mlp, quantile=0.8,
+                             xi_norm=0, refine_on=0, fp64_level=-1, include_interior=False,
+                             mem="device", fields=ALL, bands_per_thread=0, wait_timeout_ms=2000.0,
+                             capacity=None):
+        """air_render_batch_learned: batched images with the learned proposal;
+        returns (one result dict per view, stats summed over the views)."""
+        _check(lib().air_set_stream(self._h, _stream()))
+        _check(lib().air_mlp_set_stream(mlp._h, _stream()))
+        p = Params(int(base_res), int(max_level), float(xi_crit), int(xi_norm), int(refine_on),
+                   int(fp64_level), 1 if include_interior else 0)
+        o = BatchOpts(int(bands_per_thread), 0, float(wait_timeout_ms), 0)
+        lo = LearnedOpts(float(quantile))
+        stats = LearnedStats()
+        hints = getattr(self, "_batch_hint", {})
+        caps = [capacity or hints.get(k, 4 * base_res * base_res) for k in range(len(views))]
+        st, ims, outs = _batch_call(self, views, p, o, caps, mem, fields, (mlp, lo, stats))
+        if st == AIR_ERR_CAPACITY and all(im.n_out > 0 for im in ims):
+            caps = [max(int(im.n_out), 1) for im in ims]
+            st, ims, outs = _batch_call(self, views, p, o, caps, mem, fields, (mlp, lo, stats))
+        self._raster_src = None
+        _check(st)
+        self._batch_hint = {k: int(im.n_out) for k, im in enumerate(ims)}
+        sd = {f: getattr(stats, f) for f, _ in LearnedStats._fields_}
+        return [self._result(im, out) for im, out in zip(ims, outs)], sd
+
     def learn_samples(self, view, base_res, max_level, xi_crit, xi_norm=0, refine_on=0,
                       fp64_level=-1, labels=True):
         """(x, y): features [n0^2, 16] (BF16 bits as int16) and depth labels
@@ -602,7 +633,7 @@ class Grid:
         return out
 
 
-def _batch_call(grid, views, p, opts, caps, mem, fields):
+def _batch_call(grid, views, p, opts, caps, mem, fields, learned=None):
     ims, outs = [], []
     for c in caps:
         im, out = grid._alloc(c, mem, fields)
@@ -610,7 +641,12 @@ def _batch_call(grid, views, p, opts, caps, mem, fields):
         outs.append(out)
     arr_v = (View * len(views))(*[_view(v) for v in views])
     arr_i = (Image * len(views))(*ims)
-    st = lib().air_render_batch(grid._h, arr_v, len(views), C.byref(p), C.byref(opts), arr_i)
+    if learned is None:
+        st = lib().air_render_batch(grid._h, arr_v, len(views), C.byref(p), C.byref(opts), arr_i)
+    else:
+        mlp, lo, stats = learned
+        st = lib().air_render_batch_learned(grid._h, arr_v, len(views), C.byref(p), C.byref(opts),
+                                            mlp._h, C.byref(lo), arr_i, C.byref(stats))
     return st, arr_i, outs
 
 

@@ -310,6 +310,105 @@ air_status render_fixed(air_grid *g, const air_view *view, int32_t res, int32_t 
   return AIR_OK;
 }
 
+air_status level_maps(air_grid *g, int n0, int Lm, int32_t **out) {
+  Workspace &w = g->ws;
+  *out = nullptr;
+  const size_t map_bytes = sizeof(int32_t) * (size_t)level_map_offset(n0, Lm);
+  if (map_bytes == 0) return AIR_OK;
+  bool fits = w.lmap_b >= map_bytes;
+  if (!fits) {
+    size_t fr = 0, tot = 0;
+    CU_TRY(cudaMemGetInfo(&fr, &tot));
+    fits = (double)map_bytes <= 0.25 * (double)fr;
+    if (fits) CU_TRY(ensure((void **)&w.lmap, &w.lmap_b, map_bytes));
+  }
+  if (fits) {
+    CU_TRY(cudaMemsetAsync(w.lmap, 0xff, map_bytes, g->stream));
+    *out = w.lmap;
+  }
+  return AIR_OK;
+}
+
+bool pyramid_fits(air_grid *g, int64_t bound) {
+  Workspace &w = g->ws;
+  const int nb = g->gv.n_bands;
+  if (w.cap >= bound && w.n_bands == nb) return true;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const double need = ((double)bound - (double)w.cap) * (31.0 + 4.0 * nb);
+  return need <= 0.5 * (double)fr;
+}
+
+air_status sweep_loop_device(air_grid *g, const Camera &cam, const air_params *pr, int64_t nbase,
+                             int64_t m, int64_t bound, int64_t open_max, const MarchTune &tune,
+                             int march_launches, int32_t *lmap, const Proposal *prop,
+                             SweepState *fin) {
+  Workspace &w = g->ws;
+  cudaStream_t st = g->stream;
+  TreeView t = w.tree(pr->base_res, pr->max_level);
+  // Steps iii-v with every count on the device: each sweep's kernels read
+  // the open-list length, the flag count and the node count from the
+  // device state, so the host queues sweep after sweep without waiting.
+  // It reads the state back two sweeps behind, only to learn that the
+  // loop has ended; the (at most two) sweeps queued past the end find
+  // `done` set and do nothing.
+  if (!w.d_sweep) CU_TRY(cudaMalloc((void **)&w.d_sweep, sizeof(SweepState)));
+  if (!w.h_sweep) CU_TRY(cudaMallocHost((void **)&w.h_sweep, 3 * sizeof(SweepState)));
+  for (int k = 0; k < 2; ++k)
+    if (!w.ev_sweep[k]) CU_TRY(cudaEventCreateWithFlags(&w.ev_sweep[k], cudaEventDisableTiming));
+  SweepState &s0 = w.h_sweep[2];
+  std::memset(&s0, 0, sizeof(SweepState));
+  s0.n = nbase;
+  s0.m = m;
+  s0.done = m == 0;
+  CU_TRY(cudaMemcpyAsync(w.d_sweep, &s0, sizeof(SweepState), cudaMemcpyHostToDevice, st));
+  // the fused scan and balance only set flags: the base pixels' start at zero
+  CU_TRY(cudaMemsetAsync(w.flag, 0, sizeof(uint32_t) * (size_t)nbase, st));
+  int32_t *const open2[2] = {w.open[0], w.open[1]};
+  const int64_t nb_cap = scan_blocks(open_max);
+  RaySource ds{};
+  ds.mode = 2; ds.n0 = pr->base_res; ds.lvl = t.lvl; ds.pi = t.pi; ds.pj = t.pj; ds.sweep = w.d_sweep;
+  if (prop) {
+    ds.use_prop = 1;
+    ds.prop = *prop;
+  }
+  RayOut ro{t.N, t.I, t.cap, t.steps, t.p};
+  constexpr int kAhead = 2;
+  // every sweep refines at least one pixel
+  const int64_t max_sweeps = (bound - nbase) / 4 + kAhead + 1;
+  int64_t q = 0;
+  for (;; ++q) {
+    if (q >= kAhead) {
+      CU_TRY(cudaEventSynchronize(w.ev_sweep[q % kAhead]));
+      if (w.h_sweep[q % kAhead].done) break;
+    }
+    if (q > max_sweeps) return set_error(AIR_ERR_NUMERIC, "sweep loop did not end");
+    // step iii: scan and balance in one pass (counted as the scan phase)
+    CU_TRY(prof_open(g, AIR_PHASE_SCAN, 1));
+    CU_TRY(launch_sweep_scan_balance(t, open2, w.d_sweep, pr->xi_crit, pr->xi_norm, pr->refine_on,
+                                     w.flag, w.d_err, st, lmap));
+    CU_TRY(prof_close(g));
+    CU_TRY(prof_open(g, AIR_PHASE_REFINE, 3));
+    CU_TRY(launch_sweep_count(t, open2, w.d_sweep, w.flag, w.bcount, w.boff, nb_cap, st));
+    CU_TRY(launch_sweep_emit(t, open2, w.d_sweep, w.flag, w.boff, nb_cap, st, lmap));
+    CU_TRY(prof_close(g));
+    // step ii on the new pixels (or their values from the proposal); the
+    // march's last block (or the band sum after it) moves the state on
+    CU_TRY(prof_open(g, AIR_PHASE_MARCH, march_launches));
+    CU_TRY(launch_march(g->gv, cam, ds, ro, tune, st));
+    CU_TRY(prof_close(g));
+    CU_TRY(cudaMemcpyAsync(&w.h_sweep[q % kAhead], w.d_sweep, sizeof(SweepState),
+                           cudaMemcpyDeviceToHost, st));
+    CU_TRY(cudaEventRecord(w.ev_sweep[q % kAhead], st));
+  }
+  CU_TRY(cudaStreamSynchronize(st));
+  *fin = w.h_sweep[(q - 1) % kAhead];
+  return AIR_OK;
+}
+
 air_status render_adaptive(air_grid *g, const air_view *view, const air_params *pr, air_image *im,
                            float *spectra, int64_t spectra_cap, const air_shard *shard) {
   g->raster.ok = false;  // the workspace tree is about to change
@@ -437,13 +536,7 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
     // be sized for the whole image pyramid at once (no growth mid-loop); a
     // render whose pyramid would take more than half of the free device
     // memory reads the counts back sweep by sweep and grows on demand.
-    bool dev_loop = !streamed && !sharded;
-    if (dev_loop && !(w.cap >= bound && w.n_bands == nb)) {
-      size_t fr = 0, tot = 0;
-      CU_TRY(cudaMemGetInfo(&fr, &tot));
-      const double need = (double)bound * (31.0 + 4.0 * nb) - (double)w.cap * (31.0 + 4.0 * nb);
-      dev_loop = need <= 0.5 * (double)fr;
-    }
+    const bool dev_loop = !streamed && !sharded && pyramid_fits(g, bound);
     if ((s = ensure_nodes(g, dev_loop ? bound : std::min<int64_t>(bound, std::max<int64_t>(4 * nbase, w.cap)),
                           0, bound, !streamed))) return s;
     t = w.tree(n0, Lm);
@@ -464,74 +557,13 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
     int cur = 0;
     int64_t m = Lm > 0 ? nbase : 0;
     CU_TRY(launch_list_init(w.open[0], m, st));
-    // level maps (levels 1 .. Lm - 1) for the stencil and balance lookups,
-    // unless they would take more than a quarter of the free device memory
     int32_t *lmap = nullptr;
-    const size_t map_bytes = sizeof(int32_t) * (size_t)level_map_offset(n0, Lm);
-    if (map_bytes > 0) {
-      bool fits = w.lmap_b >= map_bytes;
-      if (!fits) {
-        size_t fr = 0, tot = 0;
-        CU_TRY(cudaMemGetInfo(&fr, &tot));
-        fits = (double)map_bytes <= 0.25 * (double)fr;
-        if (fits) CU_TRY(ensure((void **)&w.lmap, &w.lmap_b, map_bytes));
-      }
-      if (fits) {
-        lmap = w.lmap;
-        CU_TRY(cudaMemsetAsync(lmap, 0xff, map_bytes, st));
-      }
-    }
+    if ((s = level_maps(g, n0, Lm, &lmap))) return s;
     if (dev_loop) {
-      // Steps iii-v with every count on the device: each sweep's kernels read
-      // the open-list length, the flag count and the node count from the
-      // device state, so the host queues sweep after sweep without waiting.
-      // It reads the state back two sweeps behind, only to learn that the
-      // loop has ended; the (at most two) sweeps queued past the end find
-      // `done` set and do nothing.
-      if (!w.d_sweep) CU_TRY(cudaMalloc((void **)&w.d_sweep, sizeof(SweepState)));
-      if (!w.h_sweep) CU_TRY(cudaMallocHost((void **)&w.h_sweep, 3 * sizeof(SweepState)));
-      for (int k = 0; k < 2; ++k)
-        if (!w.ev_sweep[k]) CU_TRY(cudaEventCreateWithFlags(&w.ev_sweep[k], cudaEventDisableTiming));
-      SweepState &s0 = w.h_sweep[2];
-      std::memset(&s0, 0, sizeof(SweepState));
-      s0.n = nbase;
-      s0.m = m;
-      s0.done = m == 0;
-      CU_TRY(cudaMemcpyAsync(w.d_sweep, &s0, sizeof(SweepState), cudaMemcpyHostToDevice, st));
-      // the fused scan and balance only set flags: the base pixels' start at zero
-      CU_TRY(cudaMemsetAsync(w.flag, 0, sizeof(uint32_t) * (size_t)nbase, st));
-      int32_t *const open2[2] = {w.open[0], w.open[1]};
-      const int64_t nb_cap = scan_blocks(open_max);
-      RaySource ds{};
-      ds.mode = 2; ds.n0 = n0; ds.lvl = t.lvl; ds.pi = t.pi; ds.pj = t.pj; ds.sweep = w.d_sweep;
-      constexpr int kAhead = 2;
-      // every sweep refines at least one pixel
-      const int64_t max_sweeps = (bound - nbase) / 4 + kAhead + 1;
-      int64_t q = 0;
-      for (;; ++q) {
-        if (q >= kAhead) {
-          CU_TRY(cudaEventSynchronize(w.ev_sweep[q % kAhead]));
-          if (w.h_sweep[q % kAhead].done) break;
-        }
-        if (q > max_sweeps) return set_error(AIR_ERR_NUMERIC, "sweep loop did not end");
-        // step iii: scan and balance in one pass (counted as the scan phase)
-        CU_TRY(prof_open(g, AIR_PHASE_SCAN, 1));
-        CU_TRY(launch_sweep_scan_balance(t, open2, w.d_sweep, pr->xi_crit, pr->xi_norm, pr->refine_on,
-                                         w.flag, w.d_err, st, lmap));
-        CU_TRY(prof_close(g));
-        CU_TRY(prof_open(g, AIR_PHASE_REFINE, 3));
-        CU_TRY(launch_sweep_count(t, open2, w.d_sweep, w.flag, w.bcount, w.boff, nb_cap, st));
-        CU_TRY(launch_sweep_emit(t, open2, w.d_sweep, w.flag, w.boff, nb_cap, st, lmap));
-        CU_TRY(prof_close(g));
-        // step ii on the new pixels; the march's last block (or the band sum
-        // after it) moves the state on to the next sweep
-        if ((s = march_nodes(t, ds, tune, march_launches))) return s;
-        CU_TRY(cudaMemcpyAsync(&w.h_sweep[q % kAhead], w.d_sweep, sizeof(SweepState),
-                               cudaMemcpyDeviceToHost, st));
-        CU_TRY(cudaEventRecord(w.ev_sweep[q % kAhead], st));
-      }
-      CU_TRY(cudaStreamSynchronize(st));
-      const SweepState &fin = w.h_sweep[(q - 1) % kAhead];
+      SweepState fin;
+      if ((s = sweep_loop_device(g, cam, pr, nbase, m, bound, open_max, tune, march_launches, lmap,
+                                 nullptr, &fin)))
+        return s;
       n = fin.n;
       n_refined = fin.n_refined;
       sweeps = fin.sweeps;

@@ -159,19 +159,63 @@ __global__ void __launch_bounds__(kBatchBlock) k_air_batch(BatchArgs a) {
   const int lane = threadIdx.x & 31;
 
   // step i: the base image of every view, view-major, row-major within a view
+  // (mode 2 continues from the base images a mode-1 launch traced)
   const int64_t nbase = (int64_t)V * nn0;
-  for (int64_t k = gtid; k < nbase; k += gstride) {
-    const int v = (int)(k / nn0);
-    const int64_t r = k - (int64_t)v * nn0;
-    t.lvl[k] = 0;
-    t.pi[k] = (int32_t)(r % n0);
-    t.pj[k] = (int32_t)(r / n0);
-    t.child[k] = -1;
-    a.view[k] = (int16_t)v;
+  if (a.mode != 2) {
+    for (int64_t k = gtid; k < nbase; k += gstride) {
+      const int v = (int)(k / nn0);
+      const int64_t r = k - (int64_t)v * nn0;
+      t.lvl[k] = 0;
+      t.pi[k] = (int32_t)(r % n0);
+      t.pj[k] = (int32_t)(r / n0);
+      t.child[k] = -1;
+      a.view[k] = (int16_t)v;
+    }
+    if (!grid_sync(a.ctl, nblk + (a.stall ? 1u : 0u), a.timeout_ns)) return;
   }
-  if (!grid_sync(a.ctl, nblk + (a.stall ? 1u : 0u), a.timeout_ns)) return;
 
-  int64_t first = 0, n = nbase;
+  int64_t first = a.mode == 2 ? nbase : 0, n = nbase;
+  if (a.mode == 2 && a.P > 0) {
+    // the proposal wave of every view: (ray, band chunk) items from the queue
+    const unsigned long long items = (unsigned long long)a.P * (unsigned long long)a.chunks;
+    for (;;) {
+      unsigned long long b = 0;
+      if (lane == 0) b = atomicAdd(&a.ctl->q_head, 32ull);
+      b = __shfl_sync(0xffffffffu, b, 0);
+      if (b >= items) break;
+      const unsigned long long it = b + lane;
+      if (it < items) {
+        const int chunk = (int)(it / (unsigned long long)a.P);
+        const int64_t q = (int64_t)(it - (unsigned long long)chunk * a.P);
+        const int b0 = chunk * NBT;
+        BandCtx bc;
+        bc.tab = tab + b0 * tstride;
+        bc.tstride = tstride;
+        bc.nbh = min(NBT, nb - b0);
+        BandRegs<NBT> br;
+        band_regs<NBT>(br, g.kappa, g.invkappa, b0, bc.nbh);
+        const RayGeom rg = a.geoms[a.pview[q]];
+        RTState<NBT> st;
+        trace_ray<NBT, AMR, FMT>(st, g, rg, a.plvl[q], a.ppi[q], a.ppj[q], a.fp64_level, bc, br);
+        if (chunk == 0) {
+          a.pN[q] = st.N;
+          a.psteps[q] = st.steps;
+        }
+#pragma unroll
+        for (int c = 0; c < NBT; ++c)
+          if (c < bc.nbh) a.pI[(int64_t)(b0 + c) * a.P + q] = st.I[c];
+        if (a.chunks == 1) {
+          float p = 0.f;
+#pragma unroll
+          for (int c = 0; c < NBT; ++c)
+            if (c < bc.nbh) p += st.I[c];
+          a.pp[q] = p;
+        }
+      }
+    }
+    if (!grid_sync(a.ctl, nblk, a.timeout_ns)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->q_head = 0ull;
+  }
   int sweep = 0;
   for (;; ++sweep) {
     // step ii: trace the rays added last sweep, all views and band chunks
@@ -183,11 +227,37 @@ __global__ void __launch_bounds__(kBatchBlock) k_air_batch(BatchArgs a) {
       b = __shfl_sync(0xffffffffu, b, 0);
       if (b >= items) break;
       const unsigned long long it = b + lane;
-      if (it < items) {
-        const int chunk = (int)(it / (unsigned long long)cnt_r);
-        const int64_t k = first + (int64_t)(it - (unsigned long long)chunk * cnt_r);
-        const int v = a.view[k];
-        const int b0 = chunk * NBT;
+      bool todo = it < items;
+      int chunk = 0, v = 0, b0 = 0;
+      int64_t k = 0;
+      if (todo) {
+        chunk = (int)(it / (unsigned long long)cnt_r);
+        k = first + (int64_t)(it - (unsigned long long)chunk * cnt_r);
+        v = a.view[k];
+        b0 = chunk * NBT;
+      }
+      if (todo && a.mode == 2) {
+        // the pixel's values from its view's proposal wave when the wave
+        // traced it (the same trace, so the same bits); else trace it
+        const int L = t.lvl[k], i = t.pi[k], j = t.pj[k];
+        const int bi = i >> L, bj = j >> L;
+        const int64_t pb = (int64_t)v * nn0 + (int64_t)bj * n0 + bi;
+        if (L <= a.pdepth[pb]) {
+          const int64_t q = a.poff[pb] + prop_level_offset(L) + (int64_t)(j - (bj << L)) * (1 << L) +
+                            (i - (bi << L));
+          if (chunk == 0) {
+            t.N[k] = a.pN[q];
+            t.steps[k] = a.psteps[q];
+          }
+          const int nbh = min(NBT, nb - b0);
+          for (int c = 0; c < nbh; ++c) t.I[(int64_t)(b0 + c) * t.cap + k] = a.pI[(int64_t)(b0 + c) * a.P + q];
+          if (a.chunks == 1) t.p[k] = a.pp[q];
+          todo = false;
+        } else if (chunk == 0) {
+          atomicAdd(&a.ctl->fb_rays, 1ull);
+        }
+      }
+      if (todo) {
         BandCtx bc;
         bc.tab = tab + b0 * tstride;
         bc.tstride = tstride;
@@ -200,6 +270,7 @@ __global__ void __launch_bounds__(kBatchBlock) k_air_batch(BatchArgs a) {
         if (chunk == 0) {
           t.N[k] = st.N;
           t.steps[k] = st.steps;
+          if (a.mode == 1) a.maxlev[k] = (uint8_t)st.maxlev;
         }
 #pragma unroll
         for (int q = 0; q < NBT; ++q)
@@ -222,6 +293,15 @@ __global__ void __launch_bounds__(kBatchBlock) k_air_batch(BatchArgs a) {
         t.p[k] = s;
       }
       if (!grid_sync(a.ctl, nblk, a.timeout_ns)) return;
+    }
+    if (a.mode == 1) {
+      // the base images are traced (and their band sums): the host computes
+      // the features and the proposal, then launches mode 2
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctl->n_nodes = n;
+        a.ctl->sweeps = 0;
+      }
+      return;
     }
     // step iii: scan, then balance
     for (int64_t k = gtid; k < n; k += gstride)
@@ -457,7 +537,8 @@ static int default_batch_bands_per_thread(int nb) {
 }
 
 air_status render_batch(air_grid *g, const air_view *views, int32_t V, const air_params *pr,
-                        const air_batch_opts *opts, air_image *outs) {
+                        const air_batch_opts *opts, air_image *outs, air_mlp *mlp,
+                        const air_learned_opts *lopts, air_learned_stats *stats) {
   g->raster.ok = false;  // the workspace tree is about to change
   if (!views || !outs || !pr) return set_error(AIR_ERR_ARG, "views, params and outs must not be NULL");
   if (V < 1 || V > kBatchMaxViews) return set_error(AIR_ERR_ARG, "n_views must be in [1, %d]", kBatchMaxViews);
@@ -555,11 +636,66 @@ air_status render_batch(air_grid *g, const air_view *views, int32_t V, const air
     a.refined = bw.refined;
     a.vsweeps = bw.vsweeps;
     a.timeout_ns = (long long)(op.wait_timeout_ms * 1e6);
+    CU_TRY(cudaMemcpyAsync(bw.geoms, bw.h_geoms, sizeof(RayGeom) * V, cudaMemcpyHostToDevice, st));
+    g->prof.used = 0;
+    if (mlp) {
+      // learned proposal: the base images (mode 1), the network's proposal
+      // for every view, then every proposal wave and the sweeps (mode 2)
+      LearnWork &lw = g->learn;
+      const double q = (lopts && lopts->quantile > 0.0 && lopts->quantile <= 1.0) ? lopts->quantile : 0.8;
+      CU_TRY(ensure((void **)&lw.maxlev, &lw.maxlev_b, (size_t)nbase));
+      a.mode = 1;
+      a.maxlev = lw.maxlev;
+      for (int phase = 1; phase <= 2; ++phase) {
+        if (phase == 2) {
+          int64_t P = 0;
+          if ((s = batch_proposal(g, V, pr, mlp, q, lw.maxlev, &P))) return s;
+          a.mode = 2;
+          a.maxlev = nullptr;
+          a.pdepth = lw.depth;
+          a.poff = lw.off;
+          a.plvl = lw.plvl;
+          a.ppi = lw.ppi;
+          a.ppj = lw.ppj;
+          a.pview = lw.pview;
+          a.P = P;
+          a.pN = lw.pN;
+          a.pI = lw.pI;
+          a.pp = lw.pp;
+          a.psteps = lw.psteps;
+          if (stats) {
+            std::memset(stats, 0, sizeof(*stats));
+            stats->proposed_rays = P;
+          }
+        }
+        CU_TRY(prof_open(g, AIR_PHASE_BATCH, 1));
+        CU_TRY(cudaMemsetAsync(bw.ctl, 0, sizeof(BatchCtl), st));
+        if (phase == 1) {
+          CU_TRY(cudaMemsetAsync(bw.refined, 0, sizeof(int64_t) * V, st));
+          CU_TRY(cudaMemsetAsync(bw.vsweeps, 0, sizeof(int32_t) * V, st));
+        }
+        CU_TRY(launch(a, grid, smem, st));
+        CU_TRY(prof_close(g));
+        CU_TRY(cudaMemcpyAsync(bw.h_ctl, bw.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st));
+        CU_TRY(cudaStreamSynchronize(st));
+        if (bw.h_ctl->err & kErrTimeout)
+          return set_error(AIR_ERR_TIMEOUT, "batched kernel: a grid barrier wait exceeded %.0f ms", op.wait_timeout_ms);
+        if (bw.h_ctl->err & kErrBalance) return set_error(AIR_ERR_NUMERIC, "balance closure overflowed its stack");
+        if (bw.h_ctl->err & kErrCapacity) break;
+      }
+      const BatchCtl c = *bw.h_ctl;
+      if (c.err & kErrCapacity) {
+        if (c.need > bound) return set_error(AIR_ERR_NUMERIC, "quadtree exceeds its bound");
+        want = std::min<int64_t>(bound, std::max<int64_t>(2 * w.cap, 2 * c.need));
+        continue;
+      }
+      if (stats) stats->fallback_rays = (int64_t)c.fb_rays;
+      done = true;
+      continue;
+    }
     // the graph holds: reset of the control words, the cooperative launch
     const bool same = bw.exec && !std::memcmp(&bw.key, &a, sizeof(BatchArgs)) && bw.key_grid == grid &&
                       bw.key_smem == smem && bw.key_nbt == nbt;
-    CU_TRY(cudaMemcpyAsync(bw.geoms, bw.h_geoms, sizeof(RayGeom) * V, cudaMemcpyHostToDevice, st));
-    g->prof.used = 0;
     CU_TRY(prof_open(g, AIR_PHASE_BATCH, 1));
     if (op.use_graph) {
       if (!same) {
@@ -617,6 +753,16 @@ air_status render_batch(air_grid *g, const air_view *views, int32_t V, const air
   std::vector<int32_t> vsw(V);
   CU_TRY(cudaMemcpy(refined.data(), bw.refined, sizeof(int64_t) * V, cudaMemcpyDeviceToHost));
   CU_TRY(cudaMemcpy(vsw.data(), bw.vsweeps, sizeof(int32_t) * V, cudaMemcpyDeviceToHost));
+  if (mlp && stats) {
+    int64_t traced = 0;  // nodes beyond the base images: from the wave or traced after it
+    for (int v = 0; v < V; ++v) traced += 4 * refined[v];
+    stats->used_rays = traced - stats->fallback_rays;
+    stats->wasted_rays = stats->proposed_rays - stats->used_rays;
+    int32_t mx = 0;
+    for (int v = 0; v < V; ++v) mx = std::max(mx, vsw[v]);
+    stats->sweeps = mx;
+    stats->waves = 2;  // the base images, then the proposal waves and sweeps in one launch
+  }
   const int all = pr->include_interior;
   // sizes and capacities
   std::vector<int64_t> n_out(V);
@@ -744,4 +890,15 @@ extern "C" air_status air_render_batch(air_grid *g, const air_view *views, int32
   air::set_error(AIR_OK, "");
   if (!g) return air::set_error(AIR_ERR_ARG, "grid is NULL");
   return air::render_batch(g, views, n_views, params, opts, outs);
+}
+
+extern "C" air_status air_render_batch_learned(air_grid *g, const air_view *views, int32_t n_views,
+                                               const air_params *params, const air_batch_opts *opts,
+                                               air_mlp *mlp, const air_learned_opts *lopts,
+                                               air_image *outs, air_learned_stats *stats) {
+  air::set_error(AIR_OK, "");
+  if (!g) return air::set_error(AIR_ERR_ARG, "grid is NULL");
+  if (!mlp) return air::set_error(AIR_ERR_ARG, "mlp is NULL");
+  if (opts && opts->test_stall_barrier) return air::set_error(AIR_ERR_ARG, "test_stall_barrier is for air_render_batch");
+  return air::render_batch(g, views, n_views, params, opts, outs, mlp, lopts, stats);
 }

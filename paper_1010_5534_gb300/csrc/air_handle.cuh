@@ -86,6 +86,7 @@ struct BatchCtl {
   long long need;
   int sweeps;
   unsigned int err;
+  unsigned long long fb_rays;  // learned mode: pixels the proposal missed, traced in sweeps
 };
 
 struct BatchArgs {
@@ -101,6 +102,21 @@ struct BatchArgs {
   int64_t *refined;      // [V]
   int32_t *vsweeps;      // [V]
   long long timeout_ns;
+  // learned proposal (air_render_batch_learned): mode 0 runs every step;
+  // mode 1 traces the base images only (and the deepest brick level each
+  // base ray crossed, for the features); mode 2 continues from the traced
+  // base images: it traces every view's proposal wave, then runs the sweeps,
+  // copying a new pixel's values from the wave where it traced the pixel
+  int mode;
+  uint8_t *maxlev;       // [V n0^2] (mode 1)
+  const int8_t *pdepth;  // [V n0^2] proposed depth per base pixel (mode 2)
+  const int64_t *poff;   // [V n0^2] first proposal ray of the pixel's subtree
+  const int8_t *plvl;    // [P] proposal rays: level, pixel, view
+  const int32_t *ppi, *ppj;
+  const int16_t *pview;
+  int64_t P;
+  float *pN, *pI, *pp;   // [P], [n_bands][P], [P] traced values of the wave
+  uint32_t *psteps;      // [P]
 };
 
 // Buffers and the captured graph of batched renders.
@@ -125,7 +141,7 @@ struct BatchWork {
   size_t key_smem = 0;
 };
 
-// Buffers of the learned-proposal render.
+// Buffers of the learned-proposal render (single view and batched).
 struct LearnWork {
   float *tau0 = nullptr, *xi_p = nullptr, *xi_n = nullptr, *logits = nullptr;
   uint8_t *maxlev = nullptr;
@@ -135,6 +151,8 @@ struct LearnWork {
   int32_t *label = nullptr, *ppi = nullptr, *ppj = nullptr, *list = nullptr;
   float *pN = nullptr, *pI = nullptr, *pp = nullptr;
   uint32_t *psteps = nullptr, *missing = nullptr;
+  int16_t *pview = nullptr;  // batched: view of each proposal ray
+  size_t pview_b = 0;
   unsigned long long *counters = nullptr;
   size_t tau0_b = 0, xi_p_b = 0, xi_n_b = 0, logits_b = 0, maxlev_b = 0, x_b = 0, depth_b = 0,
          plvl_b = 0, off_b = 0, label_b = 0, ppi_b = 0, ppj_b = 0, list_b = 0, pN_b = 0, pI_b = 0,
@@ -205,8 +223,11 @@ air_status init_scalars(Workspace &w);
 // Node arrays for `need` nodes (the first `keep` preserved); with_I = false
 // leaves out the per-band intensities (streamed spectra keep them elsewhere).
 air_status ensure_nodes(air_grid *g, int64_t need, int64_t keep, int64_t bound, bool with_I = true);
+// mlp set: the batched render with the learned proposal (lopts, stats may be NULL).
 air_status render_batch(air_grid *g, const air_view *views, int32_t n_views,
-                        const air_params *params, const air_batch_opts *opts, air_image *outs);
+                        const air_params *params, const air_batch_opts *opts, air_image *outs,
+                        air_mlp *mlp = nullptr, const air_learned_opts *lopts = nullptr,
+                        air_learned_stats *stats = nullptr);
 // spectra (page-locked host, [n_bands][spectra_cap]) set: streamed spectra.
 // shard set: the rays of every sweep split over ranks (air_render_adaptive_sharded).
 air_status render_adaptive(air_grid *g, const air_view *view, const air_params *pr, air_image *im,
@@ -218,6 +239,26 @@ air_status output_tree(air_grid *g, const Camera &cam, const air_params *pr, air
                        int64_t n, int64_t n_refined, int32_t sweeps,
                        const float *spectra_dev = nullptr, int64_t spectra_cap = 0);
 air_status mlp_forward(air_mlp *m, const uint16_t *x, int64_t n, float *logits, cudaStream_t st);
+// The learned proposal of the V base images traced in the workspace (nodes
+// view-major), with the deepest brick level of each base ray in maxlev:
+// features, the network, the proposed depths and the proposal rays
+// (g->learn: depth, off, plvl, ppi, ppj, pview and room for the traced
+// values). *P: number of proposal rays.
+air_status batch_proposal(air_grid *g, int V, const air_params *pr, air_mlp *mlp, double q,
+                          const uint8_t *maxlev, int64_t *P);
+// Level maps of the single-view tree, reset (NULL if they do not fit).
+air_status level_maps(air_grid *g, int n0, int Lm, int32_t **out);
+// Whether the node arrays can be sized for a whole image pyramid of `bound`
+// nodes (at most half the free device memory beyond what is held).
+bool pyramid_fits(air_grid *g, int64_t bound);
+// Steps iii-v of one view with every count on the device, over the tree in
+// the workspace (nodes [0, nbase) traced, open[0] holding the first m
+// leaves; node arrays sized for `bound`); prop: values of new pixels from a
+// learned proposal wave where it traced them, or NULL. *fin: the final state.
+air_status sweep_loop_device(air_grid *g, const Camera &cam, const air_params *pr, int64_t nbase,
+                             int64_t m, int64_t bound, int64_t open_max, const MarchTune &tune,
+                             int march_launches, int32_t *lmap, const Proposal *prop,
+                             SweepState *fin);
 // The march configuration of this handle's tuning.
 MarchTune march_tune(const air_grid *g, int fp64_level);
 air_status render_fixed(air_grid *g, const air_view *view, int32_t res, int32_t fp64_level,

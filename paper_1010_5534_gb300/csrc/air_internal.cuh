@@ -51,6 +51,28 @@ struct Camera {
 
 struct SweepState;
 
+// A learned depth proposal traced in one wave (air_learned.cu): base pixel b
+// of an n0 x n0 image was proposed to depth depth[b], and every pixel of its
+// subtree to that depth was traced, level by level and row-major within a
+// level, from ray off[b] on. Values of proposal ray q: N[q], I[b * stride + q],
+// p[q], steps[q].
+struct Proposal {
+  const int8_t *depth;
+  const int64_t *off;
+  const float *N, *I, *p;
+  const uint32_t *steps;
+  int64_t stride;
+};
+
+// Rays in the full subtree of depth d below one pixel: 4 + 16 + ... + 4^d.
+__host__ __device__ __forceinline__ int64_t prop_subtree(int d) {
+  return ((int64_t)1 << (2 * d + 2)) / 3 - 1;
+}
+// Offset of level L (1..d) inside such a subtree.
+__host__ __device__ __forceinline__ int64_t prop_level_offset(int L) {
+  return L <= 1 ? 0 : prop_subtree(L - 1);
+}
+
 // Ray list: explicit nodes (level, i, j) of an n0 base image, the implicit
 // pixels of a res x res fixed image, or the new nodes of a sweep whose count
 // stays on the device.
@@ -65,6 +87,8 @@ struct RaySource {
   SweepState *sweep;    // mode 2: rays [S->n, S->n + 4 S->tot[0]), none once S->done;
                         // blocks take 128-ray chunks from S->ray_ctr[band chunk]
   int advance;          // mode 2: the launch's last block moves S on to the next sweep
+  int use_prop;         // mode 2: copy a new pixel's values from `prop` when the
+  Proposal prop;        // proposal traced it; trace only the pixels it missed
 };
 
 struct RayOut {

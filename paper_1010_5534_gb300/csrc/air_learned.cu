@@ -58,7 +58,7 @@ __global__ void k_base_xi(const float *p, const float *N, int n0, float *xi_p, f
 // 13 max xi(N) of the neighbours   14 p / max of p over 3x3   15 1
 __global__ void k_features(const float *p, const float *N, const float *tau0, const uint8_t *maxlev,
                            const float *xi_p, const float *xi_n, int n0, int grid_levels,
-                           uint16_t *x) {
+                           uint16_t *x, const float *kappa) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n0 * n0) return;
   const int i = k % n0, j = k / n0;
@@ -98,7 +98,8 @@ __global__ void k_features(const float *p, const float *N, const float *tau0, co
   f[4] = fabsf(gv) / (sp + tiny);
   f[5] = (pmax - pmin) / (pmax + tiny);
   f[6] = (nmax - nmin) / (nmax + tiny);
-  f[7] = fminf(tau0 ? tau0[k] : 0.f, 10.f) * 0.1f;
+  // band-0 optical depth: the march's kappa_0 N, or formed here the same way
+  f[7] = fminf(tau0 ? tau0[k] : (kappa ? kappa[0] * nv[4] : 0.f), 10.f) * 0.1f;
   f[8] = maxlev ? (float)maxlev[k] / (float)max(1, grid_levels) : 0.f;
   f[9] = (float)emit * 0.125f;
   f[10] = fminf(fmaxf(log10f(nv[4] + tiny) * 0.1f, -3.f), 3.f);
@@ -155,10 +156,10 @@ __global__ void k_decide(const float *logits, int n, int max_level, float q, int
   depth[k] = (int8_t)min(d, max_level);
 }
 
-// Rays in the full subtree of depth d below one pixel: 4 + 16 + ... + 4^d.
-__host__ __device__ __forceinline__ int64_t subtree(int d) { return ((int64_t)1 << (2 * d + 2)) / 3 - 1; }
-// Offset of level L (1..d) inside such a subtree.
-__device__ __forceinline__ int64_t level_offset(int L) { return L <= 1 ? 0 : subtree(L - 1); }
+// Subtree sizes and level offsets of the proposal layout: prop_subtree,
+// prop_level_offset (air_internal.cuh).
+__host__ __device__ __forceinline__ int64_t subtree(int d) { return prop_subtree(d); }
+__device__ __forceinline__ int64_t level_offset(int L) { return prop_level_offset(L); }
 
 // Per block of kScanItems base pixels: proposal rays.
 __global__ void __launch_bounds__(256) k_prop_count(const int8_t *depth, int64_t nb, int32_t *bcount) {
@@ -201,15 +202,21 @@ __global__ void __launch_bounds__(256) k_prop_offsets(const int8_t *depth, int64
 // The proposal rays: one warp per base pixel, its lanes striding over the
 // pixel's subtree (level by level, row-major within a level), so the writes
 // are coalesced and no thread carries a whole subtree.
+// Base pixels of several views lie view-major (pixel k of view k / n0^2);
+// pview (may be NULL) receives each proposal ray's view.
 __global__ void __launch_bounds__(256) k_prop_fill(const int8_t *depth, int64_t nb, int n0,
                                                    const int64_t *off, int8_t *plvl, int32_t *ppi,
-                                                   int32_t *ppj) {
+                                                   int32_t *ppj, int16_t *pview) {
   const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (k >= nb) return;
   const int d = depth[k];
   const int64_t base = off[k], size = subtree(d);
-  const int bi = (int)(k % n0), bj = (int)(k / n0);
+  const int64_t nn0 = (int64_t)n0 * n0;
+  const int64_t r0 = k % nn0;
+  const int bi = (int)(r0 % n0), bj = (int)(r0 / n0);
+  if (pview)
+    for (int64_t r = lane; r < size; r += 32) pview[base + r] = (int16_t)(k / nn0);
   for (int64_t r = lane; r < size; r += 32) {
     int L = 1;
     while (L < d && r >= level_offset(L + 1)) ++L;
@@ -309,9 +316,63 @@ static air_status base_and_features(air_grid *g, const Camera &cam, const air_pa
   CU_TRY(prof_open(g, AIR_PHASE_LEARN, 2));
   k_base_xi<<<nblk(nbase, 256), 256, 0, st>>>(t.p, t.N, n0, lw.xi_p, lw.xi_n);
   k_features<<<nblk(nbase, 256), 256, 0, st>>>(t.p, t.N, lw.tau0, lw.maxlev, lw.xi_p, lw.xi_n, n0,
-                                               g->gv.kind == AIR_GRID_AMR ? g->gv.Lm : 0, x);
+                                               g->gv.kind == AIR_GRID_AMR ? g->gv.Lm : 0, x, nullptr);
   CU_TRY(cudaGetLastError());
   CU_TRY(prof_close(g));
+  return AIR_OK;
+}
+
+air_status batch_proposal(air_grid *g, int V, const air_params *pr, air_mlp *mlp, double q,
+                          const uint8_t *maxlev, int64_t *P_out) {
+  Workspace &w = g->ws;
+  LearnWork &lw = g->learn;
+  cudaStream_t st = g->stream;
+  const int n0 = pr->base_res, Lm = pr->max_level;
+  const int64_t nn0 = (int64_t)n0 * n0, nbase = (int64_t)V * nn0;
+  const int nb = g->gv.n_bands;
+  TreeView t = w.tree(n0, Lm);
+  CU_TRY(ensure((void **)&lw.xi_p, &lw.xi_p_b, sizeof(float) * nbase));
+  CU_TRY(ensure((void **)&lw.xi_n, &lw.xi_n_b, sizeof(float) * nbase));
+  CU_TRY(ensure((void **)&lw.x, &lw.x_b, sizeof(uint16_t) * nbase * kFeat));
+  CU_TRY(ensure((void **)&lw.logits, &lw.logits_b, sizeof(float) * nbase * 5));
+  CU_TRY(ensure((void **)&lw.depth, &lw.depth_b, nbase));
+  CU_TRY(ensure((void **)&lw.off, &lw.off_b, sizeof(int64_t) * nbase));
+  CU_TRY(ensure((void **)&w.bcount, &w.bcount_b, sizeof(int32_t) * scan_blocks(nbase)));
+  CU_TRY(ensure((void **)&w.boff, &w.boff_b, sizeof(int64_t) * scan_blocks(nbase)));
+  // features of every view's base image (view v: nodes [v n0^2, (v + 1) n0^2))
+  CU_TRY(prof_open(g, AIR_PHASE_LEARN, 2 * V + 5));
+  for (int v = 0; v < V; ++v) {
+    const int64_t o = (int64_t)v * nn0;
+    k_base_xi<<<nblk(nn0, 256), 256, 0, st>>>(t.p + o, t.N + o, n0, lw.xi_p + o, lw.xi_n + o);
+    k_features<<<nblk(nn0, 256), 256, 0, st>>>(t.p + o, t.N + o, nullptr, maxlev + o, lw.xi_p + o,
+                                               lw.xi_n + o, n0, g->gv.kind == AIR_GRID_AMR ? g->gv.Lm : 0,
+                                               lw.x + o * kFeat, g->gv.kappa);
+  }
+  CU_TRY(cudaGetLastError());
+  air_status s = mlp_forward(mlp, lw.x, nbase, lw.logits, st);
+  if (s) return s;
+  k_decide<<<nblk(nbase, 256), 256, 0, st>>>(lw.logits, (int)nbase, Lm, (float)q, lw.depth);
+  const int64_t nbb = scan_blocks(nbase);
+  k_prop_count<<<(unsigned)nbb, 256, 0, st>>>(lw.depth, nbase, w.bcount);
+  CU_TRY(cudaGetLastError());
+  CU_TRY(launch_scan_offsets(w.bcount, nbb, w.boff, w.d_total, st));
+  CU_TRY(cudaMemcpyAsync(w.h_total, w.d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CU_TRY(cudaStreamSynchronize(st));
+  const int64_t P = *w.h_total, P1 = std::max<int64_t>(P, 1);
+  CU_TRY(ensure((void **)&lw.plvl, &lw.plvl_b, P1));
+  CU_TRY(ensure((void **)&lw.ppi, &lw.ppi_b, sizeof(int32_t) * P1));
+  CU_TRY(ensure((void **)&lw.ppj, &lw.ppj_b, sizeof(int32_t) * P1));
+  CU_TRY(ensure((void **)&lw.pview, &lw.pview_b, sizeof(int16_t) * P1));
+  CU_TRY(ensure((void **)&lw.pN, &lw.pN_b, sizeof(float) * P1));
+  CU_TRY(ensure((void **)&lw.pI, &lw.pI_b, sizeof(float) * P1 * nb));
+  CU_TRY(ensure((void **)&lw.pp, &lw.pp_b, sizeof(float) * P1));
+  CU_TRY(ensure((void **)&lw.psteps, &lw.psteps_b, sizeof(uint32_t) * P1));
+  k_prop_offsets<<<(unsigned)nbb, 256, 0, st>>>(lw.depth, nbase, w.boff, lw.off);
+  k_prop_fill<<<nblk(nbase * 32, 256), 256, 0, st>>>(lw.depth, nbase, n0, lw.off, lw.plvl, lw.ppi, lw.ppj,
+                                                     lw.pview);
+  CU_TRY(cudaGetLastError());
+  CU_TRY(prof_close(g));
+  *P_out = P;
   return AIR_OK;
 }
 
@@ -377,7 +438,11 @@ air_status render_learned(air_grid *g, const air_view *view, const air_params *p
   if (bound > INT32_MAX) return set_error(AIR_ERR_ARG, "image pyramid exceeds 2^31 nodes");
   CU_TRY(ensure((void **)&w.bcount, &w.bcount_b, sizeof(int32_t) * scan_blocks(bound)));
   CU_TRY(ensure((void **)&w.boff, &w.boff_b, sizeof(int64_t) * scan_blocks(bound)));
-  if ((s = ensure_nodes(g, std::min<int64_t>(bound, std::max<int64_t>(4 * nbase, w.cap)), 0, bound))) return s;
+  // the replay runs with its counts on the device when the node arrays can
+  // hold the whole pyramid (as the plain render's loop)
+  const bool dev_loop = pyramid_fits(g, bound);
+  if ((s = ensure_nodes(g, dev_loop ? bound : std::min<int64_t>(bound, std::max<int64_t>(4 * nbase, w.cap)),
+                        0, bound))) return s;
   CU_TRY(ensure((void **)&lw.x, &lw.x_b, sizeof(uint16_t) * nbase * kFeat));
   CU_TRY(ensure((void **)&lw.logits, &lw.logits_b, sizeof(float) * nbase * 5));
   CU_TRY(ensure((void **)&lw.depth, &lw.depth_b, nbase));
@@ -410,7 +475,8 @@ air_status render_learned(air_grid *g, const air_view *view, const air_params *p
   CU_TRY(ensure((void **)&lw.pp, &lw.pp_b, sizeof(float) * std::max<int64_t>(P, 1)));
   CU_TRY(ensure((void **)&lw.psteps, &lw.psteps_b, sizeof(uint32_t) * std::max<int64_t>(P, 1)));
   k_prop_offsets<<<(unsigned)nbb, 256, 0, st>>>(lw.depth, nbase, w.boff, lw.off);
-  k_prop_fill<<<nblk(nbase * 32, 256), 256, 0, st>>>(lw.depth, nbase, n0, lw.off, lw.plvl, lw.ppi, lw.ppj);
+  k_prop_fill<<<nblk(nbase * 32, 256), 256, 0, st>>>(lw.depth, nbase, n0, lw.off, lw.plvl, lw.ppi, lw.ppj,
+                                                     nullptr);
   CU_TRY(cudaGetLastError());
   CU_TRY(prof_close(g));
   const MarchTune tune = march_tune(g, pr->fp64_level);
@@ -439,6 +505,23 @@ air_status render_learned(air_grid *g, const air_view *view, const air_params *p
   int cur = 0;
   int64_t mo = Lm > 0 ? nbase : 0;
   CU_TRY(launch_list_init(w.open[0], mo, st));
+  if (dev_loop) {
+    // the device-count sweep loop; new pixels copy their values from the
+    // proposal wave where it traced them, the march traces the rest
+    int32_t *lmap = nullptr;
+    if ((s = level_maps(g, n0, Lm, &lmap))) return s;
+    const Proposal prop{lw.depth, lw.off, lw.pN, lw.pI, lw.pp, lw.psteps, std::max<int64_t>(P, 1)};
+    SweepState fin;
+    if ((s = sweep_loop_device(g, cam, pr, nbase, mo, bound, open_max, tune, march_launches, lmap, &prop,
+                               &fin)))
+      return s;
+    n = fin.n;
+    n_refined = fin.n_refined;
+    sweeps = fin.sweeps;
+    fallback = (int64_t)fin.fb_total;
+    waves += fin.fb_waves;
+    mo = 0;
+  }
   for (;;) {
     if (mo == 0) break;
     CU_TRY(prof_open(g, AIR_PHASE_SCAN, 1));
@@ -530,7 +613,7 @@ air_status render_learned(air_grid *g, const air_view *view, const air_params *p
 void free_learn(air_grid *g) {
   LearnWork &l = g->learn;
   void *ps[] = {l.tau0, l.xi_p, l.xi_n, l.logits, l.maxlev, l.x, l.depth, l.plvl, l.off, l.label,
-                l.ppi, l.ppj, l.list, l.pN, l.pI, l.pp, l.psteps, l.missing, l.counters};
+                l.ppi, l.ppj, l.list, l.pN, l.pI, l.pp, l.psteps, l.missing, l.counters, l.pview};
   for (void *p : ps)
     if (p) cudaFree(p);
   l = LearnWork{};

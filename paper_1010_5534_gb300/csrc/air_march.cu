@@ -28,6 +28,26 @@ __device__ __forceinline__ void march_one(const GridView &g, const RayGeom &rg, 
                                           const RayOut &out, int fp64_level, const BandCtx &bc,
                                           const BandRegs<NBT> &br, int chunk, int b0, int nbh,
                                           int64_t k) {
+  if (src.use_prop) {
+    // the pixel's values from the proposal wave when it traced the pixel
+    // (the same trace, so the same bits); else trace it here
+    const Proposal &pr = src.prop;
+    const int L = src.lvl[k], i = src.pi[k], j = src.pj[k];
+    const int bi = i >> L, bj = j >> L, b = bj * src.n0 + bi;
+    if (L <= pr.depth[b]) {
+      const int64_t q = pr.off[b] + prop_level_offset(L) + (int64_t)(j - (bj << L)) * (1 << L) +
+                        (i - (bi << L));
+      if (chunk == 0) {
+        out.N[k] = pr.N[q];
+        out.steps[k] = pr.steps[q];
+      }
+      for (int c = 0; c < nbh; ++c)
+        out.I[(int64_t)(b0 + c) * out.stride + k] = pr.I[(int64_t)(b0 + c) * pr.stride + q];
+      if (out.p && gridDim.y == 1) out.p[k] = pr.p[q];
+      return;
+    }
+    if (chunk == 0) atomicAdd(&src.sweep->fb_sweep, 1ull);
+  }
   RTState<NBT> st;
   trace_ray<NBT, AMR, FMT, DIR>(st, g, rg, src.lvl[k], src.pi[k], src.pj[k], fp64_level, bc, br);
   if (chunk == 0) {

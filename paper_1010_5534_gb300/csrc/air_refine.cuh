@@ -69,6 +69,10 @@ struct SweepState {
   int done;             // the last scan flagged nothing (or nothing is left to scan)
   unsigned blocks_done; // blocks of the sweep's last kernel that have finished
   unsigned long long ray_ctr[kMaxBands];  // march work counters, one per band chunk
+  // with a learned proposal: pixels it missed, traced this sweep / in all
+  // sweeps, and the sweeps that traced any
+  unsigned long long fb_sweep, fb_total;
+  int fb_waves;
 };
 
 // After the new pixels are traced: n, m, cur, sweeps and n_refined move on to
@@ -84,6 +88,11 @@ __device__ __forceinline__ void sweep_advance(SweepState *S) {
   if (S->m == 0) S->done = 1;  // no leaf below the top level is left
   for (int b = 0; b < kMaxBands; ++b) S->ray_ctr[b] = 0ull;
   S->blocks_done = 0u;
+  if (S->fb_sweep) {
+    S->fb_total += S->fb_sweep;
+    S->fb_waves += 1;
+    S->fb_sweep = 0ull;
+  }
 }
 
 // Called by thread 0 of every block of the sweep's last kernel as the block

@@ -153,13 +153,37 @@ __device__ __forceinline__ uint32_t xi_flag(const TreeView &t, NodeLookup look, 
   const int i = t.pi[k], j = t.pj[k];
   const int nl = t.n0 << L;
   int q[9];
+  if (look.lmap && L >= 1) {
+    // level maps: the eight level-L entries are independent loads, issued
+    // together; a neighbour missing at level L (a coarser leaf covers it, at
+    // most one level up in a balanced tree) is looked up level by level
+    const int32_t *mL = look.lmap + level_map_offset(t.n0, L);
 #pragma unroll
-  for (int dj = -1; dj <= 1; ++dj)
+    for (int dj = -1; dj <= 1; ++dj)
 #pragma unroll
-    for (int di = -1; di <= 1; ++di) {
-      const int ii = min(max(i + di, 0), nl - 1), jj = min(max(j + dj, 0), nl - 1);
-      q[3 * (dj + 1) + (di + 1)] = (di == 0 && dj == 0) ? (int)k : look(t, L, ii, jj);
-    }
+      for (int di = -1; di <= 1; ++di) {
+        const int ii = min(max(i + di, 0), nl - 1), jj = min(max(j + dj, 0), nl - 1);
+        q[3 * (dj + 1) + (di + 1)] = (di == 0 && dj == 0) ? (int)k : __ldg(mL + (int64_t)jj * nl + ii);
+      }
+#pragma unroll
+    for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+      for (int di = -1; di <= 1; ++di) {
+        const int m = 3 * (dj + 1) + (di + 1);
+        if (q[m] < 0) {
+          const int ii = min(max(i + di, 0), nl - 1), jj = min(max(j + dj, 0), nl - 1);
+          q[m] = map_deepest(t, look.lmap, L - 1, ii >> 1, jj >> 1);
+        }
+      }
+  } else {
+#pragma unroll
+    for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+      for (int di = -1; di <= 1; ++di) {
+        const int ii = min(max(i + di, 0), nl - 1), jj = min(max(j + dj, 0), nl - 1);
+        q[3 * (dj + 1) + (di + 1)] = (di == 0 && dj == 0) ? (int)k : look(t, L, ii, jj);
+      }
+  }
   uint32_t f = 0;
   float v[9];
   double s[9];

@@ -51,6 +51,17 @@ def same(a, b, what):
     np.testing.assert_array_equal(np_(a["band_flux"]), np_(b["band_flux"]))
 
 
+def same_batched(a, b, what):
+    """As `same`, but band fluxes of batched renders are FP64 atomic sums
+    (equal up to summation order)."""
+    for k in KEYS:
+        x, y = np_(a[k]), np_(b[k])
+        assert x.shape == y.shape and (x == y).all(), (what, k)
+    for k in ("n_out", "n_leaves", "n_rays", "n_sweeps", "n_steps"):
+        assert a[k] == b[k], (what, k)
+    np.testing.assert_allclose(np_(a["band_flux"]), np_(b["band_flux"]), rtol=1e-12)
+
+
 def test_training_reduced_the_loss(setup):
     s, g, net, hist = setup
     assert hist[-1] < 0.7 * hist[0]
@@ -109,3 +120,33 @@ def test_trained_network_saves_waves(setup):
     assert np.mean(waves_t) < np.mean(waves_plain)
     assert np.mean(waste_t) < np.mean(waste_z)
     zero.close()
+
+
+@pytest.mark.parametrize("q,bpt", [(0.8, 0), (0.3, 1), (1.0, 2)])
+def test_batched_learned_equals_plain_batched(setup, q, bpt):
+    """air_render_batch_learned: every view's image is bitwise the plain
+    batched render's (itself equal to the single-view render), whatever the
+    proposal quantile and band split; the proposal traces most of the image
+    in its wave."""
+    s, g, net, hist = setup
+    vs = [scenes.axis_view("+z")] + scenes.random_views(77, 4)
+    plain = g.render_batch(vs, N0, LM, XC, include_interior=True, bands_per_thread=bpt)
+    lrn, st = g.render_batch_learned(vs, N0, LM, XC, net, quantile=q, include_interior=True,
+                                     bands_per_thread=bpt)
+    for k, (a, b) in enumerate(zip(lrn, plain)):
+        same_batched(a, b, f"view {k} q {q} bpt {bpt}")
+    traced = sum(r["n_rays"] - N0 * N0 for r in plain)
+    assert st["used_rays"] + st["fallback_rays"] == traced
+    assert st["used_rays"] + st["wasted_rays"] == st["proposed_rays"]
+    if q <= 0.8:
+        assert st["used_rays"] > 0.5 * traced, st
+
+
+def test_batched_learned_large_view_count(setup):
+    """Twenty views in one batched learned render: same images as plain batched."""
+    s, g, net, hist = setup
+    vs = scenes.random_views(91, 20)
+    plain = g.render_batch(vs, N0, LM, XC)
+    lrn, st = g.render_batch_learned(vs, N0, LM, XC, net)
+    for k, (a, b) in enumerate(zip(lrn, plain)):
+        same_batched(a, b, f"view {k}")
