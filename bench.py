@@ -220,11 +220,16 @@ def _timed(fn, st):
 
 def run_batch(args):
     """Batched AIR: the cone grid with 16 bands (0.5-10 keV) at 64 random views,
-    one persistent launch per render, against the same views one by one."""
+    one persistent launch per render, against the same views one by one. Under
+    torchrun (N > 1) the views are sharded over the ranks (view v on rank v mod
+    N, no data-path collective) and only the sharded batch is timed."""
     import torch
     import paper_1010_5534_gb300 as air
     air.build()
     W = WORKLOAD
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        return run_batch_sharded(args, world)
     sc = scenes.cone_shock_amr(W["seed"], n_base=W["n_base"], brick=W["brick"], levels=W["levels"],
                                n_bands=16, e_lo=0.5, e_hi=10.0)
     g = air.Grid(sc)
@@ -272,6 +277,50 @@ def run_batch(args):
                       "flux_rel_err_vs_fixed_views_0_1": ferr}), flush=True)
 
 
+def run_batch_sharded(args, world):
+    """The 64-view, 16-band batch sharded by view over `world` ranks: each rank
+    renders its views in one persistent launch per step; per-view summaries are
+    gathered once at the end (weak scaling in views per rank)."""
+    import torch
+    import torch.distributed as dist
+    import paper_1010_5534_gb300 as air
+    from paper_1010_5534_gb300 import shard
+    rank, local = int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+    dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    W = WORKLOAD
+    sc = scenes.cone_shock_amr(W["seed"], n_base=W["n_base"], brick=W["brick"], levels=W["levels"],
+                               n_bands=16, e_lo=0.5, e_hi=10.0)
+    g = air.Grid(sc)
+    vs = scenes.random_views(3, 64)
+    mine = shard.shard_views(len(vs), rank, world)
+    my_views = [vs[k] for k in mine]
+    st = torch.cuda.current_stream()
+    render = lambda: g.render_batch(my_views, W["base_res"], W["max_level"], W["xi_crit"],
+                                    fields=("band_flux",))
+    for _ in range(max(args.warmup, 1)):
+        r = render()
+    dist.barrier()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        m, r = _timed(render, st)
+        ms.append(m)
+    dist.barrier()
+    t = torch.tensor([sum(ms)], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    allv = shard.gather_summaries({k: shard.summary(x) for k, x in zip(mine, r)}, len(vs))
+    if rank == 0:
+        steps = sum(v["n_steps"] for v in allv) * args.steps
+        print(json.dumps({"workload": "batch sharded by view: cone grid, 64 views x 16 bands",
+                          "n_gpus": world, "steps": args.steps, "ms_per_step": float(t.item()) / args.steps,
+                          "value": steps / (float(t.item()) * 1e-3), "unit": UNIT, "scaling": "weak",
+                          "views_per_rank": [len(shard.shard_views(len(vs), q, world)) for q in range(world)]}),
+              flush=True)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
 def learned_batch_record(air, torch, g, vs, n0, Lm, xc, st, train_views, plain, plain_ms,
                          quantiles=(0.8,)):
     """Train the depth network on plain trees of `train_views` of grid g (outside
@@ -311,6 +360,36 @@ def learned_batch_record(air, torch, g, vs, n0, Lm, xc, st, train_views, plain, 
                 identical_to_plain_batched=all(v["identical_to_plain_batched"] for v in per_q.values()),
                 training=f"{len(train_views)} plain trees of other views of the grid, 4 epochs",
                 training_s=train_s)
+
+
+def run_mlp(args):
+    """The depth network alone: training (minibatch Adam, forward + backward)
+    and inference throughput on synthetic BF16 features and random labels
+    (the network's cost does not depend on the values), with the tensor-core
+    FLOP rate against the measured BF16 peak."""
+    import torch
+    import paper_1010_5534_gb300 as air
+    air.build()
+    n = args.mlp_samples
+    g = torch.Generator(device="cuda").manual_seed(7)
+    x = (torch.rand((n, 16), generator=g, device="cuda") * 2.0).to(torch.bfloat16).view(torch.int16)
+    y = torch.randint(0, 5, (n,), generator=g, device="cuda", dtype=torch.int32)
+    net = air.MLP(scenes.mlp_init(0, scale=1.0))
+    st = torch.cuda.current_stream()
+    net.train(x, y, batch=8192, epochs=1, lr=1e-3)
+    train_ms, _ = _timed(lambda: net.train(x, y, batch=8192, epochs=1, lr=1e-3), st)
+    net.forward(x)
+    fwd_ms, _ = _timed(lambda: net.forward(x), st)
+    mac = 16 * 64 + 64 * 64 + 64 * 5  # multiply-adds per sample, forward
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    fwd_tf = 2 * mac * n / (fwd_ms * 1e-3) / 1e12
+    train_tf = 3 * 2 * mac * n / (train_ms * 1e-3) / 1e12  # forward + two backward products
+    print(json.dumps({"workload": f"depth network 16-64-64-5, {n} samples", "train_ms_per_epoch": train_ms,
+                      "forward_ms": fwd_ms, "forward_tflops": fwd_tf, "train_tflops": train_tf,
+                      "bf16_peak_tflops": bf16, "forward_frac_of_bf16_peak": fwd_tf / bf16,
+                      "train_frac_of_bf16_peak": train_tf / bf16}), flush=True)
 
 
 def run_ring(args):
@@ -529,8 +608,13 @@ def run_large(args):
     del X, Y
     # batched with the learned proposal (the same network), per quantile
     bl = {}
+    torch.cuda.empty_cache()
     for qq in (0.3, 0.5, 0.8):
-        g.render_batch_learned(vs, n0, Lm, xc, net, quantile=qq, fields=("band_flux",))
+        try:
+            g.render_batch_learned(vs, n0, Lm, xc, net, quantile=qq, fields=("band_flux",))
+        except air.AirError as e:  # recorded, not fatal: the other records still print
+            bl[str(qq)] = {"error": str(e), "free_gb": torch.cuda.mem_get_info()[0] / 2 ** 30}
+            continue
         ms_q, (rbl, sbl) = _timed(lambda: g.render_batch_learned(vs, n0, Lm, xc, net, quantile=qq,
                                                                  fields=("band_flux",)), st)
         bl[str(qq)] = dict(
@@ -542,7 +626,7 @@ def run_large(args):
             **{k: int(v) for k, v in sbl.items() if k in ("proposed_rays", "used_rays", "wasted_rays",
                                                          "fallback_rays")})
     out["batched_learned"] = bl
-    ms_bl = min(x["ms"] for x in bl.values())
+    ms_bl = min((x["ms"] for x in bl.values() if "ms" in x), default=float("nan"))
     # fixed 8192^2 (two views timed)
     g.render_fixed(vs[0], 1024, fields=("band_flux",))
     fx = []
@@ -660,12 +744,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-proposal comparison in the default workload")
-    ap.add_argument("--workload", default="air", choices=["air", "batch", "learned", "ring", "large"],
+    ap.add_argument("--workload", default="air", choices=["air", "batch", "learned", "ring", "large", "mlp"],
                     help="air: the benchmark line (one adaptive image of the cone grid); "
                          "batch: 64 views x 16 bands in one persistent launch vs one by one; "
                          "learned: train the depth network on 2000 plain trees, evaluate")
     ap.add_argument("--seeds", type=int, default=40)
     ap.add_argument("--views", type=int, default=50)
+    ap.add_argument("--mlp-samples", type=int, default=1 << 24,
+                    help="samples of the --workload mlp run")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the one-view record of the large configuration")
     ap.add_argument("--clocks-file", default=None,
@@ -685,6 +771,8 @@ def main():
         return run_ring(args)
     if args.workload == "large":
         return run_large(args)
+    if args.workload == "mlp":
+        return run_mlp(args)
     assert args.warmup >= 3 or args.profile_case, "at least 3 warm-up steps"
 
     import torch

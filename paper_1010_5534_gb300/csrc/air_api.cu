@@ -33,7 +33,9 @@ cudaError_t ensure(void **p, size_t *have, size_t bytes) {
   *p = nullptr;
   *have = 0;
   if (bytes == 0) return cudaSuccess;
-  const size_t grow = bytes + bytes / 4;
+  // headroom for the next, slightly larger request: a quarter, a sixteenth
+  // above 4 GiB (buffers of many-band, many-view renders)
+  const size_t grow = bytes + (bytes > ((size_t)4 << 30) ? bytes / 16 : bytes / 4);
   cudaError_t e = cudaMalloc(p, grow);
   if (e == cudaSuccess) *have = grow;
   return e;
@@ -118,11 +120,12 @@ static cudaError_t regrow(T *&p, int64_t old_cap, int64_t cap, int64_t keep, int
   return cudaSuccess;
 }
 
-air_status ensure_nodes(air_grid *g, int64_t need, int64_t keep, int64_t bound, bool with_I) {
+air_status ensure_nodes(air_grid *g, int64_t need, int64_t keep, int64_t bound, bool with_I, bool exact) {
   Workspace &w = g->ws;
   const int nb = with_I ? g->gv.n_bands : -1;  // -1 tags arrays without intensities
   if (w.cap >= need && w.n_bands == nb) return AIR_OK;
-  int64_t cap = std::max<int64_t>(need, std::min<int64_t>(bound, std::max<int64_t>(2 * w.cap, need + need / 2)));
+  int64_t cap = exact ? need
+                      : std::max<int64_t>(need, std::min<int64_t>(bound, std::max<int64_t>(2 * w.cap, need + need / 2)));
   if (cap < need) cap = need;
   if (w.n_bands != nb) {
     keep = 0;

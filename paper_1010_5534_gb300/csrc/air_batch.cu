@@ -536,6 +536,23 @@ static int default_batch_bands_per_thread(int nb) {
   return 8;
 }
 
+// Node count for the next attempt of a batch that outgrew its arrays at
+// `need` nodes (more sweeps may follow): twice that, as far as half of the
+// free device memory allows, and at least a sixteenth above it.
+static int64_t batch_regrow(air_grid *g, int64_t need, int64_t bound) {
+  const double per_node = 31.0 + 4.0 * g->gv.n_bands;
+  size_t fr = 0, tot = 0;
+  int64_t roomy = 2 * need;
+  if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+    const int64_t held = g->ws.cap;  // freed when the arrays are replaced
+    const int64_t fit = (int64_t)(0.5 * (double)fr / per_node) + held;
+    roomy = std::min<int64_t>(roomy, fit);
+  } else {
+    cudaGetLastError();
+  }
+  return std::min<int64_t>(bound, std::max<int64_t>(need + need / 16, roomy));
+}
+
 air_status render_batch(air_grid *g, const air_view *views, int32_t V, const air_params *pr,
                         const air_batch_opts *opts, air_image *outs, air_mlp *mlp,
                         const air_learned_opts *lopts, air_learned_stats *stats) {
@@ -616,7 +633,9 @@ air_status render_batch(air_grid *g, const air_view *views, int32_t V, const air
   int64_t want = std::max<int64_t>(std::min<int64_t>(bound, 4 * nbase), w.cap);
   bool done = false;
   for (int attempt = 0; attempt < 8 && !done; ++attempt) {
-    if ((s = ensure_nodes(g, want, 0, bound))) return s;
+    // a batch that outgrew the node arrays is rendered again with arrays of
+    // the size it needed (and a sixteenth more), not the usual doubling
+    if ((s = ensure_nodes(g, want, 0, bound, true, attempt > 0))) return s;
     TreeView t = w.tree(n0, Lm);
     BatchArgs a{};
     a.g = g->gv;
@@ -686,7 +705,7 @@ air_status render_batch(air_grid *g, const air_view *views, int32_t V, const air
       const BatchCtl c = *bw.h_ctl;
       if (c.err & kErrCapacity) {
         if (c.need > bound) return set_error(AIR_ERR_NUMERIC, "quadtree exceeds its bound");
-        want = std::min<int64_t>(bound, std::max<int64_t>(2 * w.cap, 2 * c.need));
+        want = batch_regrow(g, c.need, bound);
         continue;
       }
       if (stats) stats->fallback_rays = (int64_t)c.fb_rays;
@@ -742,7 +761,7 @@ air_status render_batch(air_grid *g, const air_view *views, int32_t V, const air
     if (c.err & kErrBalance) return set_error(AIR_ERR_NUMERIC, "balance closure overflowed its stack");
     if (c.err & kErrCapacity) {
       if (c.need > bound) return set_error(AIR_ERR_NUMERIC, "quadtree exceeds its bound");
-      want = std::min<int64_t>(bound, std::max<int64_t>(2 * w.cap, 2 * c.need));
+      want = batch_regrow(g, c.need, bound);
       continue;
     }
     done = true;

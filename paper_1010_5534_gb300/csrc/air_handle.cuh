@@ -221,8 +221,10 @@ air_status check_image(const air_image *im);
 air_status make_camera(const air_view *v, Camera &c);
 air_status init_scalars(Workspace &w);
 // Node arrays for `need` nodes (the first `keep` preserved); with_I = false
-// leaves out the per-band intensities (streamed spectra keep them elsewhere).
-air_status ensure_nodes(air_grid *g, int64_t need, int64_t keep, int64_t bound, bool with_I = true);
+// leaves out the per-band intensities (streamed spectra keep them elsewhere);
+// exact: allocate `need` nodes, not the growth margin.
+air_status ensure_nodes(air_grid *g, int64_t need, int64_t keep, int64_t bound, bool with_I = true,
+                        bool exact = false);
 // mlp set: the batched render with the learned proposal (lopts, stats may be NULL).
 air_status render_batch(air_grid *g, const air_view *views, int32_t n_views,
                         const air_params *params, const air_batch_opts *opts, air_image *outs,
