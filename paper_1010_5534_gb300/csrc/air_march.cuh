@@ -182,14 +182,93 @@ __device__ __forceinline__ void prefetch_cell(const void *__restrict__ cells, Id
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
+// (1 - e^-x) / x for 0 <= x < 1/64 from its Taylor series truncated after
+// x^3 (remainder < x^4 / 5! < 5e-10).
+__device__ __forceinline__ float one_minus_exp_over_x_short(float x) {
+  float g = -1.0f / 24.0f;
+  g = fmaf(g, x, 1.0f / 6.0f);
+  g = fmaf(g, x, -0.5f);
+  g = fmaf(g, x, 1.0f);
+  return g;
+}
+
+// The transfer steps of a group of U column cells, all with chord ds. Inside
+// the group the column density and the band intensities are summed in plain
+// FP32 (partial sums from zero, the cell terms added with one fused
+// multiply-add each), and the group's partial sums are added to the running
+// sums with Kahan compensation; the error of a plain sum of U = 16 positive
+// terms is at most 15 u of the group's sum (u = 2^-24), so the column's sums
+// stay within about 16 u of exact. T_b at each cell is 2^(nk_b N_k) with N_k
+// the running column density plus the group's partial sum (one rounding).
+// FORM 2: every dtau of the group below 1/64 (the short series); FORM 1: below
+// 1/4 (the full series); FORM 0: the form is selected per cell and band.
+template <int NBT, int FMT, int FORM, int U>
+__device__ __forceinline__ void column_group(RTState<NBT> &r, const float (&rh)[U],
+                                             const uint32_t (&xv)[U], float ds, const BandCtx &bc,
+                                             const BandRegs<NBT> &br) {
+  float pN = 0.f, pI[NBT];
+#pragma unroll
+  for (int b = 0; b < NBT; ++b) pI[b] = 0.f;
+  const float N0 = r.N;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const float rho = rh[u];
+    const float rds = __fmul_rn(rho, ds);
+    pN = __fadd_rn(pN, rds);
+    const float Nk = __fadd_rn(N0, pN);
+    int k = 0;
+    float w = 0.f, lam1 = 1.f;
+    if (FMT == kCellXq) {
+      k = (int)(xv[u] >> kXqFracBits);
+      w = (float)(xv[u] & ((1u << kXqFracBits) - 1u)) * (1.0f / (float)(1u << kXqFracBits));
+    } else if (FMT == kCellLam) {
+      lam1 = __uint_as_float(xv[u]);
+    }
+#pragma unroll
+    for (int b = 0; b < NBT; ++b) {
+      if (NBT == 1 || b < bc.nbh) {
+        float lam = lam1;
+        if (FMT == kCellXq) {
+          const float *t = bc.tab + b * bc.tstride + k;
+          lam = fmaf(w, t[1] - t[0], t[0]);
+        }
+        const float dtau = __fmul_rn(br.kap[b], rds);
+        const float Tn = ex2_approx(__fmul_rn(br.nk[b], Nk));
+        const float rl = __fmul_rn(rho, lam);
+        float P, Q;
+        if (FORM == 2) {
+          P = __fmul_rn(rl, rds);
+          Q = __fmul_rn(r.T[b], one_minus_exp_over_x_short(dtau));
+        } else {
+          const float Ps = __fmul_rn(rl, rds);
+          const float Qs = __fmul_rn(r.T[b], one_minus_exp_over_x(dtau));
+          if (FORM == 1) {
+            P = Ps;
+            Q = Qs;
+          } else {
+            const bool small = dtau < 0.25f;
+            P = small ? Ps : __fmul_rn(rl, br.ik[b]);
+            Q = small ? Qs : __fsub_rn(r.T[b], Tn);
+          }
+        }
+        pI[b] = fmaf(P, Q, pI[b]);
+        r.T[b] = Tn;
+      }
+    }
+  }
+  kahan_add(r.N, r.cN, pN);
+#pragma unroll
+  for (int b = 0; b < NBT; ++b)
+    if (NBT == 1 || b < bc.nbh) kahan_add(r.I[b], r.cI[b], pI[b]);
+}
+
 // n cells of one column (cell idx, idx + d, ...), every one crossed whole
 // with the same chord ds: the path of a ray parallel to a grid axis, which
 // enters each block of cells through a face and leaves through the opposite
 // one. No DDA is needed. Cells are fetched U at a time (U loads in flight per
-// thread) and the transfer form is chosen per group of U cells: when
-// kmax (rho_max ds) < 1/4 for the group's largest rho, every cell's dtau =
-// kappa_b (rho ds) is below 1/4 too (FP32 rounding is monotonic), and the
-// series form alone gives the bits the per-cell selection would.
+// thread) and summed as a group (column_group); the transfer form is chosen
+// per group from kmax (rho_max ds) for the group's largest rho, which bounds
+// every cell's dtau = kappa_b (rho ds) (FP32 rounding is monotonic).
 template <int NBT, int FMT, int U, typename Idx>
 __device__ __forceinline__ void march_column(RTState<NBT> &r, const void *__restrict__ cells, Idx idx,
                                              Idx d, int n, float ds, const BandCtx &bc,
@@ -205,13 +284,10 @@ __device__ __forceinline__ void march_column(RTState<NBT> &r, const void *__rest
     float m = rh[0];
 #pragma unroll
     for (int u = 1; u < U; ++u) m = fmaxf(m, rh[u]);
-    if (br.kmax * (m * ds) < 0.25f) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) rt_term<NBT, FMT, true>(r, rh[u], xv[u], ds, bc, br);
-    } else {
-#pragma unroll
-      for (int u = 0; u < U; ++u) rt_term<NBT, FMT, false>(r, rh[u], xv[u], ds, bc, br);
-    }
+    const float dmax = br.kmax * __fmul_rn(m, ds);
+    if (dmax < 0.015625f) column_group<NBT, FMT, 2, U>(r, rh, xv, ds, bc, br);
+    else if (dmax < 0.25f) column_group<NBT, FMT, 1, U>(r, rh, xv, ds, bc, br);
+    else column_group<NBT, FMT, 0, U>(r, rh, xv, ds, bc, br);
   }
   for (; k < n; ++k) {
     float rh;
@@ -228,7 +304,7 @@ __device__ __forceinline__ void march_column(RTState<NBT> &r, const void *__rest
 // taken by the 3-axis DDA).
 template <int DIR>
 struct ColumnUnroll {
-  static constexpr int value = DIR >= 1 ? 16 : 8;
+  static constexpr int value = 16;
 };
 
 // DDA through a block of nx x ny x nz cells, entered in cell (lx, ly, lz),
