@@ -257,10 +257,13 @@ AIR_API air_status air_mlp_train(air_mlp *m, const uint16_t *x, const int32_t *y
                                  int32_t batch, int32_t epochs, float lr, double *loss_history);
 AIR_API void air_mlp_free(air_mlp *m);
 
-/* Training samples of one view: the 16 features of every base pixel
- * (x[n0*n0][16], device, BF16 bits, row-major pixels) and, if y is not NULL,
- * the depth plain AIR reaches below each base pixel (y[n0*n0], device, 0..4),
- * taken from a plain render with `params`. */
+/* Training samples of one view, four per base pixel: sample 4 b + q stands
+ * for quadrant q (level-1 pixel (2 bi + (q & 1), 2 bj + (q >> 1))) of base
+ * pixel b = bj * n0 + bi. x[4*n0*n0][16] (device, BF16 bits) receives the 16
+ * features of every sample and, if y is not NULL, y[4*n0*n0] (device) the
+ * deepest level plain AIR reaches below the sample's level-1 pixel (0 when
+ * the base pixel is not refined, 1 when that level-1 pixel is a leaf), taken
+ * from a plain render with `params`. */
 AIR_API air_status air_learn_samples(air_grid *g, const air_view *view, const air_params *params,
                                      uint16_t *x, int32_t *y);
 
@@ -276,12 +279,13 @@ typedef struct {
   int64_t fallback_rays;   /* pixels the proposal missed, traced afterwards */
   int32_t waves;           /* march launches: base + proposal + fallback waves */
   int32_t sweeps;          /* refinement sweeps (as plain AIR) */
-  int64_t under_predicted; /* base pixels whose final depth exceeded the proposal */
-  int64_t over_predicted;  /* base pixels proposed deeper than needed */
+  int64_t under_predicted; /* quadrant samples whose final depth exceeded the proposal */
+  int64_t over_predicted;  /* quadrant samples proposed deeper than needed */
 } air_learned_stats;
 
 /* Adaptive image with the learned proposal: trace the base image, run the
- * network on its features, trace every pixel of the proposed subtrees in one
+ * network on the features of every base pixel's four quadrants, trace every
+ * pixel of the proposed subtrees (each quadrant to its proposed depth) in one
  * wave, then run plain AIR (Section 2 steps iii-v) taking pixel values from
  * that wave, tracing only the pixels it missed. The image (pixels, order,
  * values) is identical to air_render_adaptive's; stats may be NULL. */
@@ -292,7 +296,7 @@ AIR_API air_status air_render_learned(air_grid *g, const air_view *view, const a
 /* Batched adaptive images with the learned proposal: air_render_batch with
  * the proposal of air_render_learned for every view. The base images of all
  * views are traced by the persistent kernel; the network proposes a depth for
- * every base pixel of every view; a second persistent launch traces every
+ * every quadrant of every base pixel of every view; a second persistent launch traces every
  * view's proposal wave from one work queue and then runs the sweeps of every
  * view, taking a new pixel's values from its view's wave where the wave
  * traced it and tracing the pixels the proposal missed. outs[v] is bitwise

@@ -479,13 +479,14 @@ class Grid:
 
     def learn_samples(self, view, base_res, max_level, xi_crit, xi_norm=0, refine_on=0,
                       fp64_level=-1, labels=True):
-        """(x, y): features [n0^2, 16] (BF16 bits as int16) and depth labels
-        [n0^2] (int32) of one view's base pixels, on the GPU."""
+        """(x, y): features [4 n0^2, 16] (BF16 bits as int16) and depth labels
+        [4 n0^2] (int32) of one view's quadrant samples (sample 4 b + q:
+        level-1 pixel q of base pixel b, row-major), on the GPU."""
         import torch
         _check(lib().air_set_stream(self._h, _stream()))
         p = Params(int(base_res), int(max_level), float(xi_crit), int(xi_norm), int(refine_on),
                    int(fp64_level), 0)
-        nb = base_res * base_res
+        nb = 4 * base_res * base_res
         x = torch.empty((nb, 16), dtype=torch.int16, device="cuda")
         y = torch.empty(nb, dtype=torch.int32, device="cuda") if labels else None
         _check(lib().air_learn_samples(self._h, C.byref(_view(view)), C.byref(p),

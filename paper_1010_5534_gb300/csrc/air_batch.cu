@@ -240,11 +240,9 @@ __global__ void __launch_bounds__(kBatchBlock) k_air_batch(BatchArgs a) {
         // the pixel's values from its view's proposal wave when the wave
         // traced it (the same trace, so the same bits); else trace it
         const int L = t.lvl[k], i = t.pi[k], j = t.pj[k];
-        const int bi = i >> L, bj = j >> L;
-        const int64_t pb = (int64_t)v * nn0 + (int64_t)bj * n0 + bi;
-        if (L <= a.pdepth[pb]) {
-          const int64_t q = a.poff[pb] + prop_level_offset(L) + (int64_t)(j - (bj << L)) * (1 << L) +
-                            (i - (bi << L));
+        const int64_t pb = (int64_t)v * nn0 + (int64_t)(j >> L) * n0 + (i >> L);
+        const int64_t q = prop_index(a.pdepth + 4 * pb, a.poff[pb], L, i, j);
+        if (q >= 0) {
           if (chunk == 0) {
             t.N[k] = a.pN[q];
             t.steps[k] = a.psteps[q];

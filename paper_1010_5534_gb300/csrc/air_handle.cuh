@@ -109,8 +109,8 @@ struct BatchArgs {
   // copying a new pixel's values from the wave where it traced the pixel
   int mode;
   uint8_t *maxlev;       // [V n0^2] (mode 1)
-  const int8_t *pdepth;  // [V n0^2] proposed depth per base pixel (mode 2)
-  const int64_t *poff;   // [V n0^2] first proposal ray of the pixel's subtree
+  const int8_t *pdepth;  // [V n0^2][4] proposed depth per quadrant of each base pixel (mode 2)
+  const int64_t *poff;   // [V n0^2] first proposal ray of each base pixel
   const int8_t *plvl;    // [P] proposal rays: level, pixel, view
   const int32_t *ppi, *ppj;
   const int16_t *pview;

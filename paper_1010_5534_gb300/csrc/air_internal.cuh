@@ -51,11 +51,15 @@ struct Camera {
 
 struct SweepState;
 
-// A learned depth proposal traced in one wave (air_learned.cu): base pixel b
-// of an n0 x n0 image was proposed to depth depth[b], and every pixel of its
-// subtree to that depth was traced, level by level and row-major within a
-// level, from ray off[b] on. Values of proposal ray q: N[q], I[b * stride + q],
-// p[q], steps[q].
+// A learned depth proposal traced in one wave (air_learned.cu). Each base
+// pixel b of an n0 x n0 image has four quadrants, its level-1 pixels
+// (2 bi + (q & 1), 2 bj + (q >> 1)), q = 0..3, and quadrant q was proposed to
+// depth depth[4 b + q] (an image level, 0..max_level). The rays traced for b,
+// from ray off[b] on: its four level-1 pixels when any quadrant's depth is at
+// least 1, then for q = 0..3 the full subtree of depth depth[4 b + q] - 1
+// below level-1 pixel q (image levels 2 .. depth[4 b + q]), level by level and
+// row-major within a level. Values of proposal ray r: N[r], I[c * stride + r]
+// (band c), p[r], steps[r].
 struct Proposal {
   const int8_t *depth;
   const int64_t *off;
@@ -71,6 +75,32 @@ __host__ __device__ __forceinline__ int64_t prop_subtree(int d) {
 // Offset of level L (1..d) inside such a subtree.
 __host__ __device__ __forceinline__ int64_t prop_level_offset(int L) {
   return L <= 1 ? 0 : prop_subtree(L - 1);
+}
+__host__ __device__ __forceinline__ int prop_max_depth(const int8_t *d4) {
+  int m = d4[0];
+  for (int q = 1; q < 4; ++q) m = d4[q] > m ? d4[q] : m;
+  return m;
+}
+// Rays of one base pixel's proposal, from its quadrant depths d4[0..3].
+__host__ __device__ __forceinline__ int64_t prop_rays(const int8_t *d4) {
+  if (prop_max_depth(d4) < 1) return 0;
+  int64_t s = 4;
+  for (int q = 0; q < 4; ++q) s += d4[q] > 1 ? prop_subtree(d4[q] - 1) : 0;
+  return s;
+}
+// Ray of pixel (L, i, j), L >= 1, in the proposal of the base pixel that
+// holds it (quadrant depths d4, first ray off), or -1 if it was not traced.
+__host__ __device__ __forceinline__ int64_t prop_index(const int8_t *d4, int64_t off, int L, int i,
+                                                       int j) {
+  if (L < 1) return -1;
+  const int i1 = i >> (L - 1), j1 = j >> (L - 1);
+  const int q = (i1 & 1) + 2 * (j1 & 1);
+  if (L == 1) return prop_max_depth(d4) >= 1 ? off + q : -1;
+  if (L > d4[q]) return -1;
+  int64_t o = off + 4;
+  for (int r = 0; r < q; ++r) o += d4[r] > 1 ? prop_subtree(d4[r] - 1) : 0;
+  const int Lr = L - 1;  // level below the quadrant's level-1 pixel
+  return o + prop_level_offset(Lr) + (int64_t)(j - (j1 << Lr)) * (1 << Lr) + (i - (i1 << Lr));
 }
 
 // Ray list: explicit nodes (level, i, j) of an n0 base image, the implicit

@@ -1,9 +1,10 @@
 // air_learned.cu -- learned refinement-depth proposal (not in the paper).
 //
 // The base image is traced as in plain AIR (Section 2 steps i-ii). A small
-// network (air_mlp.cu) reads 16 features of every base pixel and proposes the
-// depth plain AIR will refine it to; every pixel of the full subtree down to
-// that depth is traced in ONE wave. Then plain AIR runs exactly as before --
+// network (air_mlp.cu) reads 16 features of every quadrant of every base
+// pixel (its four level-1 pixels) and proposes the depth plain AIR will refine
+// that quadrant to; every pixel of the proposed subtrees is traced in ONE
+// wave (layout: Proposal, air_internal.cuh). Then plain AIR runs exactly as before --
 // scan (Eq. 2), balance, refine -- except that the values of a new pixel are
 // gathered from the proposal wave instead of being traced; pixels the proposal
 // missed are traced in a fallback wave. The paper's criterion, evaluated on
@@ -50,42 +51,55 @@ __global__ void k_base_xi(const float *p, const float *N, int n0, float *xi_p, f
   xi_n[k] = (float)base_xi(N, n0, i, j);
 }
 
-// Pass 2: the 16 features of every base pixel (scale-free where possible):
-//  0 xi(p)  1 xi(N)  2 [p > 0]  3 |Sobel_u p| / sum|p|  4 |Sobel_v p| / sum|p|
-//  5 (max - min)/max of p over 3x3   6 same for N   7 min(tau_0, 10)/10
-//  8 deepest brick level crossed / max level   9 emitting neighbours / 8
-// 10 log10(N)/10   11 log10(p)/20 (both clamped)   12 max xi(p) of the 8 neighbours
-// 13 max xi(N) of the neighbours   14 p / max of p over 3x3   15 1
+// Pass 2: the 16 features of every quadrant sample s = 4 b + q of base pixel
+// b = (i, j) (row-major), quadrant q on the side (sx, sy) = (q & 1 ? 1 : -1,
+// q & 2 ? 1 : -1); S = the three base neighbours on that side, (i + sx, j),
+// (i, j + sy) and (i + sx, j + sy), and Q = S and the pixel itself (edges
+// clamped; scale-free where possible):
+//  0 xi(p)  1 xi(N)  2 [p > 0]  3 sx Sobel_u(p) / sum|p|  4 sy Sobel_v(p) / sum|p|
+//    (3x3, the gradient towards the quadrant)
+//  5 (max - min)/max of p over Q   6 same for N   7 min(tau_0, 10)/10
+//  8 deepest brick level crossed / max level   9 emitting pixels of S / 3
+// 10 log10(N)/10   11 log10(p)/20 (both clamped)   12 max xi(p) over S
+// 13 max xi(N) over S   14 p / max of p over Q   15 1
 __global__ void k_features(const float *p, const float *N, const float *tau0, const uint8_t *maxlev,
                            const float *xi_p, const float *xi_n, int n0, int grid_levels,
                            uint16_t *x, const float *kappa) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n0 * n0) return;
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= 4 * (int64_t)n0 * n0) return;
+  const int k = (int)(s >> 2), qd = (int)(s & 3);
   const int i = k % n0, j = k / n0;
-  float pv[9], nv[9], xp = 0.f, xn = 0.f;
+  const int sx = (qd & 1) ? 1 : -1, sy = (qd & 2) ? 1 : -1;
+  float pv[9], nv[9];
 #pragma unroll
   for (int dj = -1; dj <= 1; ++dj)
 #pragma unroll
     for (int di = -1; di <= 1; ++di) {
       const int ii = min(max(i + di, 0), n0 - 1), jj = min(max(j + dj, 0), n0 - 1);
-      const int q = jj * n0 + ii, m = 3 * (dj + 1) + (di + 1);
-      pv[m] = p[q];
-      nv[m] = N[q];
-      if (m != 4) {
-        xp = fmaxf(xp, xi_p[q]);
-        xn = fmaxf(xn, xi_n[q]);
-      }
+      const int m = 3 * (dj + 1) + (di + 1);
+      pv[m] = p[jj * n0 + ii];
+      nv[m] = N[jj * n0 + ii];
     }
-  float sp = 0.f, pmax = 0.f, pmin = FLT_MAX, nmax = 0.f, nmin = FLT_MAX;
+  float sp = 0.f;
+#pragma unroll
+  for (int m = 0; m < 9; ++m) sp += fabsf(pv[m]);
+  // the side set S (its entries of the 3x3 stencil and its pixels' indices)
+  const int ms[3] = {4 + sx, 4 + 3 * sy, 4 + 3 * sy + sx};
+  const int is[3] = {min(max(i + sx, 0), n0 - 1), i, min(max(i + sx, 0), n0 - 1)};
+  const int js[3] = {j, min(max(j + sy, 0), n0 - 1), min(max(j + sy, 0), n0 - 1)};
+  float pmax = pv[4], pmin = pv[4], nmax = nv[4], nmin = nv[4], xp = 0.f, xn = 0.f;
   int emit = 0;
 #pragma unroll
-  for (int m = 0; m < 9; ++m) {
-    sp += fabsf(pv[m]);
-    pmax = fmaxf(pmax, pv[m]);
-    pmin = fminf(pmin, pv[m]);
-    nmax = fmaxf(nmax, nv[m]);
-    nmin = fminf(nmin, nv[m]);
-    if (m != 4 && pv[m] > 0.f) ++emit;
+  for (int e = 0; e < 3; ++e) {
+    const float a = pv[ms[e]], c = nv[ms[e]];
+    pmax = fmaxf(pmax, a);
+    pmin = fminf(pmin, a);
+    nmax = fmaxf(nmax, c);
+    nmin = fminf(nmin, c);
+    if (a > 0.f) ++emit;
+    const int qn = js[e] * n0 + is[e];
+    xp = fmaxf(xp, xi_p[qn]);
+    xn = fmaxf(xn, xi_n[qn]);
   }
   const float gu = (pv[2] + 2.f * pv[5] + pv[8]) - (pv[0] + 2.f * pv[3] + pv[6]);
   const float gv = (pv[6] + 2.f * pv[7] + pv[8]) - (pv[0] + 2.f * pv[1] + pv[2]);
@@ -94,14 +108,14 @@ __global__ void k_features(const float *p, const float *N, const float *tau0, co
   f[0] = xi_p[k];
   f[1] = xi_n[k];
   f[2] = pv[4] > 0.f ? 1.f : 0.f;
-  f[3] = fabsf(gu) / (sp + tiny);
-  f[4] = fabsf(gv) / (sp + tiny);
+  f[3] = (float)sx * gu / (sp + tiny);
+  f[4] = (float)sy * gv / (sp + tiny);
   f[5] = (pmax - pmin) / (pmax + tiny);
   f[6] = (nmax - nmin) / (nmax + tiny);
   // band-0 optical depth: the march's kappa_0 N, or formed here the same way
   f[7] = fminf(tau0 ? tau0[k] : (kappa ? kappa[0] * nv[4] : 0.f), 10.f) * 0.1f;
   f[8] = maxlev ? (float)maxlev[k] / (float)max(1, grid_levels) : 0.f;
-  f[9] = (float)emit * 0.125f;
+  f[9] = (float)emit * (1.f / 3.f);
   f[10] = fminf(fmaxf(log10f(nv[4] + tiny) * 0.1f, -3.f), 3.f);
   f[11] = fminf(fmaxf(log10f(pv[4] + tiny) * 0.05f, -3.f), 3.f);
   f[12] = xp;
@@ -109,22 +123,30 @@ __global__ void k_features(const float *p, const float *N, const float *tau0, co
   f[14] = pv[4] / (pmax + tiny);
   f[15] = 1.f;
 #pragma unroll
-  for (int q = 0; q < kFeat; ++q) x[(int64_t)k * kFeat + q] = f2bf(f[q]);
+  for (int c = 0; c < kFeat; ++c) x[s * kFeat + c] = f2bf(f[c]);
 }
 
-// Depth label of every base pixel: the deepest node below it (nodes [0, n));
-// the labels must be zeroed first.
+// Depth label of every quadrant sample 4 b + q: the deepest node below
+// base pixel b's level-1 pixel q (nodes [0, n)); 1 for every quadrant of a
+// refined base pixel whose level-1 pixel is a leaf; the labels must be zeroed
+// first.
 __global__ void k_depth_labels(const int8_t *lvl, const int32_t *pi, const int32_t *pj, int64_t n,
                                int n0, int32_t *label) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   // labels start at zero (the base level); children come in groups of four
-  // at n0^2 + 4 m, all of one level: the first of each group stands for it
+  // at n0^2 + 4 m, all of one level and one quadrant below level 1: the
+  // first of each group stands for it
   const int64_t nbase = (int64_t)n0 * n0;
   if (k < nbase || ((k - nbase) & 3) != 0) return;
   const int L = lvl[k];
-  const int b = (pj[k] >> L) * n0 + (pi[k] >> L);
-  atomicMax(label + b, L);
+  const int64_t b = (int64_t)(pj[k] >> L) * n0 + (pi[k] >> L);
+  if (L == 1) {
+    for (int q = 0; q < 4; ++q) atomicMax(label + 4 * b + q, 1);
+    return;
+  }
+  const int q = ((pi[k] >> (L - 1)) & 1) + 2 * ((pj[k] >> (L - 1)) & 1);
+  atomicMax(label + 4 * b + q, L);
 }
 
 // Decision: the smallest depth d whose cumulative probability reaches q.
@@ -156,25 +178,21 @@ __global__ void k_decide(const float *logits, int n, int max_level, float q, int
   depth[k] = (int8_t)min(d, max_level);
 }
 
-// Subtree sizes and level offsets of the proposal layout: prop_subtree,
-// prop_level_offset (air_internal.cuh).
-__host__ __device__ __forceinline__ int64_t subtree(int d) { return prop_subtree(d); }
-__device__ __forceinline__ int64_t level_offset(int L) { return prop_level_offset(L); }
-
-// Per block of kScanItems base pixels: proposal rays.
+// Per block of kScanItems base pixels: proposal rays (prop_rays of each
+// pixel's four quadrant depths).
 __global__ void __launch_bounds__(256) k_prop_count(const int8_t *depth, int64_t nb, int32_t *bcount) {
   __shared__ int64_t s;
   if (threadIdx.x == 0) s = 0;
   __syncthreads();
   const int64_t s0 = (int64_t)blockIdx.x * kScanItems, s1 = min(nb, s0 + kScanItems);
   int64_t c = 0;
-  for (int64_t k = s0 + threadIdx.x; k < s1; k += blockDim.x) c += subtree(depth[k]);
+  for (int64_t k = s0 + threadIdx.x; k < s1; k += blockDim.x) c += prop_rays(depth + 4 * k);
   atomicAdd((unsigned long long *)&s, (unsigned long long)c);
   __syncthreads();
   if (threadIdx.x == 0) bcount[blockIdx.x] = (int32_t)s;
 }
 
-// Offsets of every base pixel's subtree (sequential within the block by a
+// First proposal ray of every base pixel (sequential within the block by a
 // shared-memory scan).
 __global__ void __launch_bounds__(256) k_prop_offsets(const int8_t *depth, int64_t nb,
                                                       const int64_t *boff, int64_t *off) {
@@ -183,7 +201,7 @@ __global__ void __launch_bounds__(256) k_prop_offsets(const int8_t *depth, int64
   const int64_t per = (kScanItems + 255) / 256;
   const int64_t a = s0 + threadIdx.x * per, b = min(s1, a + per);
   int64_t c = 0;
-  for (int64_t k = a; k < b; ++k) c += subtree(depth[k]);
+  for (int64_t k = a; k < b; ++k) c += prop_rays(depth + 4 * k);
   part[threadIdx.x] = c;
   __syncthreads();
   for (int o = 1; o < 256; o <<= 1) {
@@ -195,13 +213,14 @@ __global__ void __launch_bounds__(256) k_prop_offsets(const int8_t *depth, int64
   int64_t run = boff[blockIdx.x] + part[threadIdx.x] - c;
   for (int64_t k = a; k < b; ++k) {
     off[k] = run;
-    run += subtree(depth[k]);
+    run += prop_rays(depth + 4 * k);
   }
 }
 
 // The proposal rays: one warp per base pixel, its lanes striding over the
-// pixel's subtree (level by level, row-major within a level), so the writes
-// are coalesced and no thread carries a whole subtree.
+// pixel's rays in the Proposal layout (the four level-1 pixels, then each
+// quadrant's subtree level by level, row-major within a level), so the
+// writes are coalesced and no thread carries a whole subtree.
 // Base pixels of several views lie view-major (pixel k of view k / n0^2);
 // pview (may be NULL) receives each proposal ray's view.
 __global__ void __launch_bounds__(256) k_prop_fill(const int8_t *depth, int64_t nb, int n0,
@@ -210,21 +229,37 @@ __global__ void __launch_bounds__(256) k_prop_fill(const int8_t *depth, int64_t 
   const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (k >= nb) return;
-  const int d = depth[k];
-  const int64_t base = off[k], size = subtree(d);
+  const int8_t *d4 = depth + 4 * k;
+  const int64_t base = off[k], size = prop_rays(d4);
   const int64_t nn0 = (int64_t)n0 * n0;
   const int64_t r0 = k % nn0;
   const int bi = (int)(r0 % n0), bj = (int)(r0 / n0);
+  int64_t qsz[4];
+  for (int q = 0; q < 4; ++q) qsz[q] = d4[q] > 1 ? prop_subtree(d4[q] - 1) : 0;
   if (pview)
     for (int64_t r = lane; r < size; r += 32) pview[base + r] = (int16_t)(k / nn0);
   for (int64_t r = lane; r < size; r += 32) {
-    int L = 1;
-    while (L < d && r >= level_offset(L + 1)) ++L;
-    const int64_t q = r - level_offset(L);
-    const int w = 1 << L;
+    int L, i, j;
+    if (r < 4) {
+      L = 1;
+      i = 2 * bi + (int)(r & 1);
+      j = 2 * bj + (int)(r >> 1);
+    } else {
+      int64_t rr = r - 4;
+      int q = 0;
+      while (q < 3 && rr >= qsz[q]) rr -= qsz[q++];
+      const int e = d4[q] - 1;  // the quadrant's subtree depth (>= 1 here)
+      int Lr = 1;
+      while (Lr < e && rr >= prop_level_offset(Lr + 1)) ++Lr;
+      const int64_t loc = rr - prop_level_offset(Lr);
+      const int w = 1 << Lr;
+      L = Lr + 1;
+      i = ((2 * bi + (q & 1)) << Lr) + (int)(loc % w);
+      j = ((2 * bj + (q >> 1)) << Lr) + (int)(loc / w);
+    }
     plvl[base + r] = (int8_t)L;
-    ppi[base + r] = (bi << L) + (int)(q % w);
-    ppj[base + r] = (bj << L) + (int)(q / w);
+    ppi[base + r] = i;
+    ppj[base + r] = j;
   }
 }
 
@@ -236,14 +271,13 @@ __global__ void k_gather(TreeView t, int64_t first, int64_t n, int n_bands, cons
   const int64_t k = first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int L = t.lvl[k], i = t.pi[k], j = t.pj[k];
-  const int bi = i >> L, bj = j >> L, b = bj * t.n0 + bi;
-  if (L > depth[b]) {
+  const int64_t b = (int64_t)(j >> L) * t.n0 + (i >> L);
+  const int64_t q = prop_index(depth + 4 * b, off[b], L, i, j);
+  if (q < 0) {
     missing[k - first] = 1u;
     return;
   }
   missing[k - first] = 0u;
-  const int w = 1 << L;
-  const int64_t q = off[b] + level_offset(L) + (int64_t)(j - (bj << L)) * w + (i - (bi << L));
   t.N[k] = pN[q];
   t.p[k] = pp[q];
   t.steps[k] = psteps[q];
@@ -275,7 +309,7 @@ __global__ void __launch_bounds__(256) k_list_missing(const uint32_t *missing, i
   }
 }
 
-// Leaves of the final tree per base pixel vs the proposal: under / over counts.
+// Final depth per quadrant sample vs the proposal: under / over counts.
 __global__ void k_pred_stats(const int32_t *label, const int8_t *depth, int nb,
                              unsigned long long *under, unsigned long long *over) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -293,7 +327,8 @@ __global__ void k_pred_stats(const int32_t *label, const int8_t *depth, int nb,
 static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 // Base image of one view traced into the quadtree workspace (nodes [0, n0^2))
-// with band-0 optical depth and deepest level, then its features -> x.
+// with band-0 optical depth and deepest level, then the features of its
+// 4 n0^2 quadrant samples -> x.
 static air_status base_and_features(air_grid *g, const Camera &cam, const air_params *pr,
                                     uint16_t *x, cudaStream_t st) {
   Workspace &w = g->ws;
@@ -315,7 +350,7 @@ static air_status base_and_features(air_grid *g, const Camera &cam, const air_pa
   CU_TRY(prof_close(g));
   CU_TRY(prof_open(g, AIR_PHASE_LEARN, 2));
   k_base_xi<<<nblk(nbase, 256), 256, 0, st>>>(t.p, t.N, n0, lw.xi_p, lw.xi_n);
-  k_features<<<nblk(nbase, 256), 256, 0, st>>>(t.p, t.N, lw.tau0, lw.maxlev, lw.xi_p, lw.xi_n, n0,
+  k_features<<<nblk(4 * nbase, 256), 256, 0, st>>>(t.p, t.N, lw.tau0, lw.maxlev, lw.xi_p, lw.xi_n, n0,
                                                g->gv.kind == AIR_GRID_AMR ? g->gv.Lm : 0, x, nullptr);
   CU_TRY(cudaGetLastError());
   CU_TRY(prof_close(g));
@@ -333,9 +368,9 @@ air_status batch_proposal(air_grid *g, int V, const air_params *pr, air_mlp *mlp
   TreeView t = w.tree(n0, Lm);
   CU_TRY(ensure((void **)&lw.xi_p, &lw.xi_p_b, sizeof(float) * nbase));
   CU_TRY(ensure((void **)&lw.xi_n, &lw.xi_n_b, sizeof(float) * nbase));
-  CU_TRY(ensure((void **)&lw.x, &lw.x_b, sizeof(uint16_t) * nbase * kFeat));
-  CU_TRY(ensure((void **)&lw.logits, &lw.logits_b, sizeof(float) * nbase * 5));
-  CU_TRY(ensure((void **)&lw.depth, &lw.depth_b, nbase));
+  CU_TRY(ensure((void **)&lw.x, &lw.x_b, sizeof(uint16_t) * 4 * nbase * kFeat));
+  CU_TRY(ensure((void **)&lw.logits, &lw.logits_b, sizeof(float) * 4 * nbase * 5));
+  CU_TRY(ensure((void **)&lw.depth, &lw.depth_b, 4 * nbase));
   CU_TRY(ensure((void **)&lw.off, &lw.off_b, sizeof(int64_t) * nbase));
   CU_TRY(ensure((void **)&w.bcount, &w.bcount_b, sizeof(int32_t) * scan_blocks(nbase)));
   CU_TRY(ensure((void **)&w.boff, &w.boff_b, sizeof(int64_t) * scan_blocks(nbase)));
@@ -344,14 +379,14 @@ air_status batch_proposal(air_grid *g, int V, const air_params *pr, air_mlp *mlp
   for (int v = 0; v < V; ++v) {
     const int64_t o = (int64_t)v * nn0;
     k_base_xi<<<nblk(nn0, 256), 256, 0, st>>>(t.p + o, t.N + o, n0, lw.xi_p + o, lw.xi_n + o);
-    k_features<<<nblk(nn0, 256), 256, 0, st>>>(t.p + o, t.N + o, nullptr, maxlev + o, lw.xi_p + o,
-                                               lw.xi_n + o, n0, g->gv.kind == AIR_GRID_AMR ? g->gv.Lm : 0,
-                                               lw.x + o * kFeat, g->gv.kappa);
+    k_features<<<nblk(4 * nn0, 256), 256, 0, st>>>(t.p + o, t.N + o, nullptr, maxlev + o, lw.xi_p + o,
+                                                   lw.xi_n + o, n0, g->gv.kind == AIR_GRID_AMR ? g->gv.Lm : 0,
+                                                   lw.x + 4 * o * kFeat, g->gv.kappa);
   }
   CU_TRY(cudaGetLastError());
-  air_status s = mlp_forward(mlp, lw.x, nbase, lw.logits, st);
+  air_status s = mlp_forward(mlp, lw.x, 4 * nbase, lw.logits, st);
   if (s) return s;
-  k_decide<<<nblk(nbase, 256), 256, 0, st>>>(lw.logits, (int)nbase, Lm, (float)q, lw.depth);
+  k_decide<<<nblk(4 * nbase, 256), 256, 0, st>>>(lw.logits, (int)(4 * nbase), Lm, (float)q, lw.depth);
   const int64_t nbb = scan_blocks(nbase);
   k_prop_count<<<(unsigned)nbb, 256, 0, st>>>(lw.depth, nbase, w.bcount);
   CU_TRY(cudaGetLastError());
@@ -393,7 +428,7 @@ air_status learn_samples(air_grid *g, const air_view *view, const air_params *pr
     if (s != AIR_OK && s != AIR_ERR_CAPACITY) return s;
     set_error(AIR_OK, "");
     TreeView t = g->ws.tree(n0, pr->max_level);
-    CU_TRY(cudaMemsetAsync(y, 0, sizeof(int32_t) * n0 * n0, st));
+    CU_TRY(cudaMemsetAsync(y, 0, sizeof(int32_t) * 4 * n0 * n0, st));
     k_depth_labels<<<nblk(g->last.n_nodes, 256), 256, 0, st>>>(t.lvl, t.pi, t.pj, g->last.n_nodes, n0, y);
     CU_TRY(cudaGetLastError());
     g->last.valid = false;
@@ -443,11 +478,11 @@ air_status render_learned(air_grid *g, const air_view *view, const air_params *p
   const bool dev_loop = pyramid_fits(g, bound);
   if ((s = ensure_nodes(g, dev_loop ? bound : std::min<int64_t>(bound, std::max<int64_t>(4 * nbase, w.cap)),
                         0, bound))) return s;
-  CU_TRY(ensure((void **)&lw.x, &lw.x_b, sizeof(uint16_t) * nbase * kFeat));
-  CU_TRY(ensure((void **)&lw.logits, &lw.logits_b, sizeof(float) * nbase * 5));
-  CU_TRY(ensure((void **)&lw.depth, &lw.depth_b, nbase));
+  CU_TRY(ensure((void **)&lw.x, &lw.x_b, sizeof(uint16_t) * 4 * nbase * kFeat));
+  CU_TRY(ensure((void **)&lw.logits, &lw.logits_b, sizeof(float) * 4 * nbase * 5));
+  CU_TRY(ensure((void **)&lw.depth, &lw.depth_b, 4 * nbase));
   CU_TRY(ensure((void **)&lw.off, &lw.off_b, sizeof(int64_t) * nbase));
-  CU_TRY(ensure((void **)&lw.label, &lw.label_b, sizeof(int32_t) * nbase));
+  CU_TRY(ensure((void **)&lw.label, &lw.label_b, sizeof(int32_t) * 4 * nbase));
   CU_TRY(ensure((void **)&lw.counters, &lw.counters_b, sizeof(unsigned long long) * 2));
   g->prof.used = 0;
   int waves = 0;
@@ -455,10 +490,10 @@ air_status render_learned(air_grid *g, const air_view *view, const air_params *p
   if ((s = base_and_features(g, cam, pr, lw.x, st))) return s;
   ++waves;
   CU_TRY(prof_open(g, AIR_PHASE_LEARN, 1));
-  if ((s = mlp_forward(mlp, lw.x, nbase, lw.logits, st))) return s;
+  if ((s = mlp_forward(mlp, lw.x, 4 * nbase, lw.logits, st))) return s;
   CU_TRY(prof_close(g));
   CU_TRY(prof_open(g, AIR_PHASE_LEARN, 5));
-  k_decide<<<nblk(nbase, 256), 256, 0, st>>>(lw.logits, (int)nbase, Lm, (float)q, lw.depth);
+  k_decide<<<nblk(4 * nbase, 256), 256, 0, st>>>(lw.logits, (int)(4 * nbase), Lm, (float)q, lw.depth);
   CU_TRY(cudaGetLastError());
   const int64_t nbb = scan_blocks(nbase);
   k_prop_count<<<(unsigned)nbb, 256, 0, st>>>(lw.depth, nbase, w.bcount);
@@ -584,10 +619,11 @@ air_status render_learned(air_grid *g, const air_view *view, const air_params *p
   CU_TRY(cudaStreamSynchronize(st));
   if (*w.h_err) return set_error(AIR_ERR_NUMERIC, "balance closure overflowed its stack");
   // statistics of the proposal against the final tree
-  CU_TRY(cudaMemsetAsync(lw.label, 0, sizeof(int32_t) * nbase, st));
+  CU_TRY(cudaMemsetAsync(lw.label, 0, sizeof(int32_t) * 4 * nbase, st));
   CU_TRY(cudaMemsetAsync(lw.counters, 0, sizeof(unsigned long long) * 2, st));
   k_depth_labels<<<nblk(n, 256), 256, 0, st>>>(t.lvl, t.pi, t.pj, n, n0, lw.label);
-  k_pred_stats<<<nblk(nbase, 256), 256, 0, st>>>(lw.label, lw.depth, (int)nbase, lw.counters, lw.counters + 1);
+  k_pred_stats<<<nblk(4 * nbase, 256), 256, 0, st>>>(lw.label, lw.depth, (int)(4 * nbase), lw.counters,
+                                                      lw.counters + 1);
   CU_TRY(cudaGetLastError());
   unsigned long long hc[2] = {0, 0};
   CU_TRY(cudaMemcpyAsync(hc, lw.counters, sizeof(hc), cudaMemcpyDeviceToHost, st));

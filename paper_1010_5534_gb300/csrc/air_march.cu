@@ -33,10 +33,9 @@ __device__ __forceinline__ void march_one(const GridView &g, const RayGeom &rg, 
     // (the same trace, so the same bits); else trace it here
     const Proposal &pr = src.prop;
     const int L = src.lvl[k], i = src.pi[k], j = src.pj[k];
-    const int bi = i >> L, bj = j >> L, b = bj * src.n0 + bi;
-    if (L <= pr.depth[b]) {
-      const int64_t q = pr.off[b] + prop_level_offset(L) + (int64_t)(j - (bj << L)) * (1 << L) +
-                        (i - (bi << L));
+    const int64_t b = (int64_t)(j >> L) * src.n0 + (i >> L);
+    const int64_t q = prop_index(pr.depth + 4 * b, pr.off[b], L, i, j);
+    if (q >= 0) {
       if (chunk == 0) {
         out.N[k] = pr.N[q];
         out.steps[k] = pr.steps[q];

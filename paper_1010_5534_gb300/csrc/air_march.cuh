@@ -99,17 +99,14 @@ __device__ __forceinline__ void rt_init(RTState<NBT> &r) {
 // Lambda (kCellLam, as float bits) or the table coordinate of T (kCellXq).
 // With dtau = 0 (kappa_b = 0 or rho = 0) the series form gives the optically
 // thin term j ds T exactly, so no separate case is needed.
-// THIN = false: both forms of the cell term are evaluated and the one for the
-// cell's dtau is selected, which keeps the loop free of divergent branches.
-// THIN = true: the caller has shown that every band's dtau < 1/4 for this
-// cell, so only the series form is evaluated -- the form the selection would
-// pick, hence the same bits.
+// Both forms of the cell term are evaluated and the one for the cell's dtau
+// is selected, which keeps the loop free of divergent branches.
 //
 // The products that feed the compensated sums (rho ds, and each form's final
 // product) are rounded explicitly (__fmul_rn), so the compiler cannot fuse
 // them into the sums' subtractions: every instantiation (band chunking, form)
 // rounds alike and gives the same bits.
-template <int NBT, int FMT, bool THIN = false>
+template <int NBT, int FMT>
 __device__ __forceinline__ void rt_term(RTState<NBT> &r, float rho, uint32_t aux, float ds,
                                         const BandCtx &bc, const BandRegs<NBT> &br) {
   const float rds = __fmul_rn(rho, ds);
@@ -134,11 +131,8 @@ __device__ __forceinline__ void rt_term(RTState<NBT> &r, float rho, uint32_t aux
       const float Tn = ex2_approx(br.nk[b] * r.N);
       const float rl = rho * lam;
       const float t_small = __fmul_rn(rl * rds, r.T[b] * one_minus_exp_over_x(dtau));
-      float term = t_small;
-      if (!THIN) {
-        const float t_large = __fmul_rn(rl * br.ik[b], r.T[b] - Tn);
-        term = dtau < 0.25f ? t_small : t_large;
-      }
+      const float t_large = __fmul_rn(rl * br.ik[b], r.T[b] - Tn);
+      const float term = dtau < 0.25f ? t_small : t_large;
       r.T[b] = Tn;
       kahan_add(r.I[b], r.cI[b], term);
     }
@@ -147,14 +141,14 @@ __device__ __forceinline__ void rt_term(RTState<NBT> &r, float rho, uint32_t aux
 
 // One cell chord of length ds >= 0 on the DDA path. A zero-length chord (a
 // ray grazing an edge or corner) adds nothing and is not counted as a step.
-// When kmax (rho ds) < 1/4 every band's dtau is below 1/4 (FP32 rounding is
-// monotonic), so the series form alone gives the bits of the selection.
+// Both transfer forms are evaluated and one selected per band: a per-cell
+// branch to the series form alone (same bits when kmax (rho ds) < 1/4) was
+// timed and made the batched 16-band renders 15% slower.
 template <int NBT, int FMT>
 __device__ __forceinline__ void rt_cell(RTState<NBT> &r, float rho, uint32_t aux, float ds,
                                         const BandCtx &bc, const BandRegs<NBT> &br) {
   r.steps += ds > 0.f ? 1u : 0u;
-  if (br.kmax * __fmul_rn(rho, ds) < 0.25f) rt_term<NBT, FMT, true>(r, rho, aux, ds, bc, br);
-  else rt_term<NBT, FMT, false>(r, rho, aux, ds, bc, br);
+  rt_term<NBT, FMT>(r, rho, aux, ds, bc, br);
 }
 
 // Cells of a block requested ahead of the march along its dominant axis.
@@ -294,7 +288,7 @@ __device__ __forceinline__ void march_column(RTState<NBT> &r, const void *__rest
     uint32_t xv;
     load_cell<FMT>(cells, idx, rh, xv);
     idx += d;
-    rt_term<NBT, FMT, false>(r, rh, xv, ds, bc, br);
+    rt_term<NBT, FMT>(r, rh, xv, ds, bc, br);
   }
 }
 

@@ -526,6 +526,8 @@ __device__ __forceinline__ double pow4_neg(int L) {
 __global__ void __launch_bounds__(256) k_flux_partial(FluxArgs a) {
   __shared__ double sh[256];
   __shared__ unsigned long long shs[256];
+  __shared__ double area[kMaxLevels];
+  if (threadIdx.x < kMaxLevels) area[threadIdx.x] = a.area0 * pow4_neg(threadIdx.x);
   const int64_t start = (int64_t)blockIdx.x * a.per_block;
   const int64_t end = min(a.n, start + a.per_block);
   double *outp = a.partial + (int64_t)blockIdx.x * (a.n_bands + 1);
@@ -542,10 +544,7 @@ __global__ void __launch_bounds__(256) k_flux_partial(FluxArgs a) {
     double s = 0.0;
     for (int64_t k = start + threadIdx.x; k < end; k += blockDim.x) {
       const bool leaf = a.child ? a.child[k] < 0 : true;
-      if (leaf) {
-        const int L = a.lvl ? a.lvl[k] : 0;
-        s += (double)a.I[(int64_t)b * a.stride + k] * a.area0 * pow4_neg(L);
-      }
+      if (leaf) s = fma((double)a.I[(int64_t)b * a.stride + k], area[a.lvl ? a.lvl[k] : 0], s);
     }
     sh[threadIdx.x] = s;
     __syncthreads();

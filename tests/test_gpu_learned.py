@@ -94,13 +94,17 @@ def test_labels_are_the_oracle_tree_depths(setup):
     v = scenes.axis_view("+z")
     x, y = g.learn_samples(v, N0, LM, XC)
     t = o.air(v, N0, LM, XC)
-    depth = np.zeros(N0 * N0, int)
+    # sample 4 b + q: the deepest level below level-1 pixel q of base pixel b
+    depth = np.zeros(4 * N0 * N0, int)
     for L, i, j in zip(t["level"], t["i"], t["j"]):
+        if L == 0:
+            continue
         b = (j >> L) * N0 + (i >> L)
-        depth[b] = max(depth[b], L)
+        q = ((i >> (L - 1)) & 1) + 2 * ((j >> (L - 1)) & 1)
+        depth[4 * b + q] = max(depth[4 * b + q], L)
     assert (np_(y) == depth).all()
     f = np_(x).view(np.uint16).astype(np.uint32) << 16
-    feats = f.view(np.float32).reshape(N0 * N0, 16)
+    feats = f.view(np.float32).reshape(4 * N0 * N0, 16)
     assert np.isfinite(feats).all() and (feats[:, 15] == 1.0).all()
     assert ((feats[:, 0] >= 0) & (feats[:, 0] <= 1)).all()
 
