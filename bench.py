@@ -935,7 +935,7 @@ def main():
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
         for _ in range(args.warmup):
-            g.render_learned(view, W["base_res"], W["max_level"], W["xi_crit"], net, quantile=0.8,
+            g.render_learned(view, W["base_res"], W["max_level"], W["xi_crit"], net, quantile=0.99,
                              capacity=cap)
         lms, waves = [], 0
         for _ in range(args.steps):
@@ -943,7 +943,7 @@ def main():
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(st)
             rl, stl = g.render_learned(view, W["base_res"], W["max_level"], W["xi_crit"], net,
-                                       quantile=0.8, capacity=cap)
+                                       quantile=0.99, capacity=cap)
             e1.record(st)
             e1.synchronize()
             lms.append(e0.elapsed_time(e1))

@@ -292,6 +292,10 @@ air_status render_fixed(air_grid *g, const air_view *view, int32_t res, int32_t 
   RaySource src{};
   src.mode = 1; src.n0 = res; src.first = 0; src.count = n;
   src.tile_w = g->tune.tile_w > 0 ? g->tune.tile_w : 8;
+  {
+    const air_status sa = axis_table(g, cam, res, 0, src);
+    if (sa) return sa;
+  }
   RayOut ro{w.fN, w.fI, n, w.fsteps, w.fp};
   g->prof.used = 0;
   CU_TRY(prof_open(g, AIR_PHASE_MARCH, nb > (g->tune.bands_per_thread > 0 ? g->tune.bands_per_thread : default_bands_per_thread(nb)) ? 2 : 1));
@@ -310,6 +314,31 @@ air_status render_fixed(air_grid *g, const air_view *view, int32_t res, int32_t 
   s = finish_out(g, im, o, n);
   if (s) return s;
   CU_TRY(prof_resolve(g));
+  return AIR_OK;
+}
+
+air_status axis_table(air_grid *g, const Camera &cam, int n0, int lmax, RaySource &src) {
+  Workspace &w = g->ws;
+  src.axtab = nullptr;
+  src.axtab_slot = 0;
+  src.axtab_byj = 0;
+  const bool same = w.ax_n0 == n0 && w.ax_lmax == lmax && !std::memcmp(&w.ax_cam, &cam, sizeof(Camera));
+  if (!same) {
+    w.ax_ok = false;
+    const int64_t slot = axis_table_slot(n0, lmax);
+    CU_TRY(ensure((void **)&w.axtab, &w.axtab_b, sizeof(int32_t) * 2 * (size_t)slot));
+    bool ok = false;
+    CU_TRY(launch_axis_table(g->gv, cam, n0, lmax, w.axtab, &w.ax_byj, &w.ax_slot, &ok, g->stream));
+    w.ax_ok = ok;
+    w.ax_cam = cam;
+    w.ax_n0 = n0;
+    w.ax_lmax = lmax;
+  }
+  if (w.ax_ok) {
+    src.axtab = w.axtab;
+    src.axtab_slot = w.ax_slot;
+    src.axtab_byj = w.ax_byj;
+  }
   return AIR_OK;
 }
 
@@ -374,6 +403,10 @@ air_status sweep_loop_device(air_grid *g, const Camera &cam, const air_params *p
   const int64_t nb_cap = scan_blocks(open_max);
   RaySource ds{};
   ds.mode = 2; ds.n0 = pr->base_res; ds.lvl = t.lvl; ds.pi = t.pi; ds.pj = t.pj; ds.sweep = w.d_sweep;
+  {
+    const air_status sa = axis_table(g, cam, pr->base_res, pr->max_level, ds);
+    if (sa) return sa;
+  }
   if (prop) {
     ds.use_prop = 1;
     ds.prop = *prop;
@@ -554,6 +587,7 @@ air_status render_adaptive(air_grid *g, const air_view *view, const air_params *
     CU_TRY(cudaMemsetAsync(w.d_err, 0, sizeof(uint32_t), st));
     RaySource src{};
     src.mode = 0; src.n0 = n0; src.lvl = t.lvl; src.pi = t.pi; src.pj = t.pj; src.first = 0; src.count = nbase;
+    if ((s = axis_table(g, cam, n0, Lm, src))) return s;
     if ((s = march_nodes(t, src, tune, march_launches))) return s;
     n = nbase;
     // open-leaf list: the base pixels, unless the base is the top level

@@ -192,7 +192,7 @@ void free_grid_impl(air_grid *g) {
   dfree(w.view);
   dfree(w.lvl); dfree(w.pi); dfree(w.pj); dfree(w.child); dfree(w.N); dfree(w.I); dfree(w.p);
   dfree(w.steps); dfree(w.flag); dfree(w.bcount); dfree(w.boff); dfree(w.d_total); dfree(w.d_err);
-  dfree(w.open[0]); dfree(w.open[1]); dfree(w.lmap);
+  dfree(w.open[0]); dfree(w.open[1]); dfree(w.lmap); dfree(w.axtab);
   w.lmap_b = 0;
   dfree(w.partial); dfree(w.d_flux); dfree(w.fN); dfree(w.fI); dfree(w.fp); dfree(w.fsteps);
   dfree(w.o_level); dfree(w.o_i); dfree(w.o_j); dfree(w.o_leaf); dfree(w.o_N); dfree(w.o_p);

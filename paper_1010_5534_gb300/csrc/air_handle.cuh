@@ -30,6 +30,13 @@ struct Workspace {
   int64_t *d_total = nullptr;  // [3]
   int32_t *open[2] = {nullptr, nullptr};  // open-leaf lists (ping-pong)
   int32_t *lmap = nullptr;                 // level maps of the single-view tree
+  // column table of the last axis view (RayGeom::tab) and what it was built for
+  int32_t *axtab = nullptr;
+  size_t axtab_b = 0;
+  Camera ax_cam{};
+  int ax_n0 = -1, ax_lmax = -1, ax_byj = 0;
+  int64_t ax_slot = 0;
+  bool ax_ok = false;
   size_t lmap_b = 0;
   size_t open_b[2] = {0, 0};
   uint32_t *d_err = nullptr;
@@ -250,6 +257,10 @@ air_status batch_proposal(air_grid *g, int V, const air_params *pr, air_mlp *mlp
                           const uint8_t *maxlev, int64_t *P);
 // Level maps of the single-view tree, reset (NULL if they do not fit).
 air_status level_maps(air_grid *g, int n0, int Lm, int32_t **out);
+// src's column table (RaySource::axtab) for a view with camera cam and pixels
+// of levels 0 .. lmax of an n0 image: built once per view and kept until the
+// view changes; left NULL when the view does not qualify.
+air_status axis_table(air_grid *g, const Camera &cam, int n0, int lmax, RaySource &src);
 // Whether the node arrays can be sized for a whole image pyramid of `bound`
 // nodes (at most half the free device memory beyond what is held).
 bool pyramid_fits(air_grid *g, int64_t bound);

@@ -119,6 +119,10 @@ struct RaySource {
   int advance;          // mode 2: the launch's last block moves S on to the next sweep
   int use_prop;         // mode 2: copy a new pixel's values from `prop` when the
   Proposal prop;        // proposal traced it; trace only the pixels it missed
+  // column table of an axis view (RayGeom::tab, levels of the n0 image), or NULL
+  const int32_t *axtab;
+  int64_t axtab_slot;
+  int axtab_byj;
 };
 
 struct RayOut {
@@ -170,6 +174,15 @@ struct DeviceGrid;  // owned by the handle (defined in air_grid.cu)
 // Streaming multiprocessors of the current device (read once; 1 if the query fails).
 int sm_count();
 
+// Entries per fixed axis of a column table for levels 0 .. lmax of an n0 image.
+inline int64_t axis_table_slot(int n0, int lmax) {
+  return (int64_t)n0 * ((((int64_t)1) << (lmax + 1)) - 1);
+}
+// Column table of an axis view (RayGeom::tab) for levels 0 .. lmax of an n0
+// image into tab (2 * axis_table_slot(n0, lmax) entries); *ok = false (and
+// nothing launched) when the view does not qualify.
+cudaError_t launch_axis_table(const GridView &g, const Camera &cam, int n0, int lmax,
+                              int32_t *tab, int *byj, int64_t *slot, bool *ok, cudaStream_t st);
 cudaError_t launch_march(const GridView &g, const Camera &cam, const RaySource &src,
                          const RayOut &out, const MarchTune &tune, cudaStream_t st);
 // Bands one thread carries when the tuning leaves it open (launch_march).

@@ -343,6 +343,10 @@ static air_status base_and_features(air_grid *g, const Camera &cam, const air_pa
   CU_TRY(launch_init_base(t, st));
   RaySource src{};
   src.mode = 0; src.n0 = n0; src.lvl = t.lvl; src.pi = t.pi; src.pj = t.pj; src.first = 0; src.count = nbase;
+  {
+    const air_status sa = axis_table(g, cam, n0, pr->max_level, src);
+    if (sa) return sa;
+  }
   RayOut ro{t.N, t.I, t.cap, t.steps, t.p, lw.tau0, lw.maxlev};
   const MarchTune tune = march_tune(g, pr->fp64_level);
   CU_TRY(prof_open(g, AIR_PHASE_MARCH, g->gv.n_bands > (tune.nbt > 0 ? tune.nbt : default_bands_per_thread(g->gv.n_bands)) ? 2 : 1));
@@ -520,6 +524,7 @@ air_status render_learned(air_grid *g, const air_view *view, const air_params *p
     // the proposal wave: every pixel of every proposed subtree
     RaySource ps{};
     ps.mode = 0; ps.n0 = n0; ps.lvl = lw.plvl; ps.pi = lw.ppi; ps.pj = lw.ppj; ps.first = 0; ps.count = P;
+    if ((s = axis_table(g, cam, n0, Lm, ps))) return s;
     RayOut po{lw.pN, lw.pI, std::max<int64_t>(P, 1), lw.psteps, lw.pp};
     CU_TRY(prof_open(g, AIR_PHASE_MARCH, march_launches));
     CU_TRY(launch_march(g->gv, cam, ps, po, tune, st));
@@ -602,6 +607,7 @@ air_status render_learned(air_grid *g, const air_view *view, const air_params *p
       CU_TRY(prof_close(g));
       RaySource fs{};
       fs.mode = 0; fs.n0 = n0; fs.lvl = t.lvl; fs.pi = t.pi; fs.pj = t.pj; fs.count = miss; fs.list = lw.list;
+      if ((s = axis_table(g, cam, n0, Lm, fs))) return s;
       RayOut fo{t.N, t.I, t.cap, t.steps, t.p};
       CU_TRY(prof_open(g, AIR_PHASE_MARCH, march_launches));
       CU_TRY(launch_march(g->gv, cam, fs, fo, tune, st));

@@ -201,7 +201,10 @@ static cudaError_t launch_t(const GridView &g, const Camera &cam, const RaySourc
   const int64_t blocks = (threads + block - 1) / block;
   if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
   const size_t smem = g.cell_fmt == kCellXq ? sizeof(float) * (size_t)(NBT * (g.n_tbins + 1)) : 0;
-  const RayGeom rg = make_geom(g, cam, src.n0);
+  RayGeom rg = make_geom(g, cam, src.n0);
+  rg.tab = src.axtab;
+  rg.tab_slot = src.axtab_slot;
+  rg.tab_byj = src.axtab_byj;
   const bool amr = g.kind == AIR_GRID_AMR;
   const int moving = (rg.Dhi[0] != 0.f) + (rg.Dhi[1] != 0.f) + (rg.Dhi[2] != 0.f);
   const int fp = tune.fp64_level;
@@ -280,6 +283,31 @@ cudaError_t launch_march(const GridView &g, const Camera &cam, const RaySource &
   if (nbt <= 4) return launch_t<4>(g, cam, src, out, tune, st);
   if (nbt <= 8) return launch_t<8>(g, cam, src, out, tune, st);
   return launch_t<16>(g, cam, src, out, tune, st);
+}
+
+// Column-table entries (axis_table_entry), one per thread.
+__global__ void k_axis_table(GridView g, RayGeom rg, int A, int byj, int n0, int64_t slot,
+                             int32_t *tab) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= 2 * slot) return;
+  const int s = x >= slot ? 1 : 0;
+  const int64_t e = x - s * slot;
+  int L = 0;
+  while ((int64_t)n0 * ((((int64_t)1) << (L + 1)) - 1) <= e) ++L;
+  const int p = (int)(e - (int64_t)n0 * ((((int64_t)1) << L) - 1));
+  tab[x] = axis_table_entry(g, rg, (A + 1 + s) % 3, L, p, (byj >> s) & 1);
+}
+
+cudaError_t launch_axis_table(const GridView &g, const Camera &cam, int n0, int lmax,
+                              int32_t *tab, int *byj, int64_t *slot, bool *ok, cudaStream_t st) {
+  const RayGeom rg = make_geom(g, cam, n0);
+  int A = 0;
+  *ok = axis_table_view(rg, &A, byj);
+  *slot = axis_table_slot(n0, lmax);
+  if (!*ok) return cudaSuccess;
+  const int64_t n = 2 * *slot;
+  k_axis_table<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, rg, A, *byj, n0, *slot, tab);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_band_sum(const float *I, int n_bands, int64_t stride, int64_t first,

@@ -176,6 +176,10 @@ __device__ __forceinline__ void prefetch_cell(const void *__restrict__ cells, Id
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
+// (1 - e^-x) / x for 0 <= x < 2^-12 to first order: 1 - x / 2 (remainder
+// < x^2 / 6 < 1e-8).
+__device__ __forceinline__ float one_minus_exp_over_x_first(float x) { return fmaf(-0.5f, x, 1.0f); }
+
 // (1 - e^-x) / x for 0 <= x < 1/64 from its Taylor series truncated after
 // x^3 (remainder < x^4 / 5! < 5e-10).
 __device__ __forceinline__ float one_minus_exp_over_x_short(float x) {
@@ -194,8 +198,11 @@ __device__ __forceinline__ float one_minus_exp_over_x_short(float x) {
 // terms is at most 15 u of the group's sum (u = 2^-24), so the column's sums
 // stay within about 16 u of exact. T_b at each cell is 2^(nk_b N_k) with N_k
 // the running column density plus the group's partial sum (one rounding).
-// FORM 2: every dtau of the group below 1/64 (the short series); FORM 1: below
-// 1/4 (the full series); FORM 0: the form is selected per cell and band.
+// FORM 3: every dtau of the group below 2^-12 (the first-order series; used
+// for one-band grids with per-cell Lambda, the format whose instantiations
+// are few enough to afford another form);
+// FORM 2: below 1/64 (the short series); FORM 1: below 1/4 (the full series);
+// FORM 0: the form is selected per cell and band.
 template <int NBT, int FMT, int FORM, int U>
 __device__ __forceinline__ void column_group(RTState<NBT> &r, const float (&rh)[U],
                                              const uint32_t (&xv)[U], float ds, const BandCtx &bc,
@@ -230,7 +237,10 @@ __device__ __forceinline__ void column_group(RTState<NBT> &r, const float (&rh)[
         const float Tn = ex2_approx(__fmul_rn(br.nk[b], Nk));
         const float rl = __fmul_rn(rho, lam);
         float P, Q;
-        if (FORM == 2) {
+        if (FORM == 3) {
+          P = __fmul_rn(rl, rds);
+          Q = __fmul_rn(r.T[b], one_minus_exp_over_x_first(dtau));
+        } else if (FORM == 2) {
           P = __fmul_rn(rl, rds);
           Q = __fmul_rn(r.T[b], one_minus_exp_over_x_short(dtau));
         } else {
@@ -279,7 +289,8 @@ __device__ __forceinline__ void march_column(RTState<NBT> &r, const void *__rest
 #pragma unroll
     for (int u = 1; u < U; ++u) m = fmaxf(m, rh[u]);
     const float dmax = br.kmax * __fmul_rn(m, ds);
-    if (dmax < 0.015625f) column_group<NBT, FMT, 2, U>(r, rh, xv, ds, bc, br);
+    if (FMT == kCellLam && dmax < 0x1p-12f) column_group<NBT, FMT, 3, U>(r, rh, xv, ds, bc, br);
+    else if (dmax < 0.015625f) column_group<NBT, FMT, 2, U>(r, rh, xv, ds, bc, br);
     else if (dmax < 0.25f) column_group<NBT, FMT, 1, U>(r, rh, xv, ds, bc, br);
     else column_group<NBT, FMT, 0, U>(r, rh, xv, ds, bc, br);
   }
@@ -398,6 +409,16 @@ struct RayGeom {
   float invDhi[3];       // 1 / Dhi, correctly rounded (0 where D = 0); for a
                          // brick at 2^s finest cells per cell, 1 / (Dhi 2^-s)
                          // is exactly invDhi 2^s
+  // Axis views whose u and v are grid axes too: the cell of every pixel
+  // column on each fixed axis, from axis_table_entry (exactly the set-up's
+  // FP64 operations, once per column instead of once per ray), or NULL.
+  // Fixed axis s = (A + 1 + s) % 3 (A the ray's axis): entries
+  // tab[s * tab_slot + tab_n0 (2^L - 1) + p] for levels L = 0, 1, ..., with
+  // p the pixel's j when bit s of tab_byj is set, else its i; -1 where the
+  // column misses the grid.
+  const int32_t *tab;
+  int64_t tab_slot;
+  int tab_n0, tab_byj;
 };
 
 // 2^-L exactly (0 <= L < 1023).
@@ -451,23 +472,69 @@ __device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? l
 // column), computed exactly as ray_setup computes them, so the cells are the
 // same; c[A] is left for the caller. Half of ray_setup's FP64 work, which
 // matters on a GPU whose FP64 rate is a small fraction of FP32's.
+//
+// With a column table (RayGeom::tab) the two cells are read from it: where u
+// and v are grid axes, x_a depends on one pixel index only (the other term is
+// an exact zero), and the table holds this function's result for every
+// column (axis_table_entry), so the cells are the same bits.
+template <int A>
+__device__ __noinline__ unsigned long long axis_cells_fp64(const GridView &g, const RayGeom &rg,
+                                                           int L, int i, int j);
+
 template <int A>
 __device__ __forceinline__ bool axis_ray_setup(const GridView &g, const RayGeom &rg, int L, int i,
                                                int j, int c[3]) {
+  if (rg.tab) {
+    const int o = rg.tab_n0 * ((1 << L) - 1);
+    const int c1 = __ldg(rg.tab + o + ((rg.tab_byj & 1) ? j : i));
+    const int c2 = __ldg(rg.tab + rg.tab_slot + o + ((rg.tab_byj & 2) ? j : i));
+    c[(A + 1) % 3] = c1;
+    c[(A + 2) % 3] = c2;
+    return c1 >= 0 && c2 >= 0;
+  }
+  // a separate function, so that none of its FP64 work is executed ahead of
+  // the branch on views that have a table
+  const unsigned long long cc = axis_cells_fp64<A>(g, rg, L, i, j);
+  const int c1 = (int)(uint32_t)cc, c2 = (int)(uint32_t)(cc >> 32);
+  c[(A + 1) % 3] = c1;
+  c[(A + 2) % 3] = c2;
+  return c1 >= 0 && c2 >= 0;
+}
+
+// The two fixed cells of pixel (L, i, j)'s ray along axis A in FP64: cell on
+// axis (A + 1) % 3 in the low word, on (A + 2) % 3 in the high word, -1 where
+// the ray misses the grid on that axis.
+template <int A>
+__device__ __noinline__ unsigned long long axis_cells_fp64(const GridView &g, const RayGeom &rg,
+                                                           int L, int i, int j) {
   const double pix = rg.pix0 * exp2_neg(L);
   const double uc = fma((double)i + 0.5, pix, -rg.H);
   const double vc = fma((double)j + 0.5, pix, -rg.H);
-  bool hit = true;
+  int c[2];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (a == A) continue;
+  for (int s = 0; s < 2; ++s) {
+    const int a = (A + 1 + s) % 3;
     const double x = fma(vc, rg.V[a], fma(uc, rg.U[a], rg.C[a]));
-    const double q = x * rg.invh[a];
+    const double q = __dmul_rn(x, rg.invh[a]);
     const double o = fma(fma(-q, rg.h[a], x), rg.invh[a], q);
-    if (!(o >= 0.0 && o < (double)g.nf[a])) hit = false;
-    c[a] = hit ? (int)o : 0;  // o >= 0: truncation is floor
+    c[s] = (o >= 0.0 && o < (double)g.nf[a]) ? (int)o : -1;  // o >= 0: truncation is floor
   }
-  return hit;
+  return (unsigned long long)(uint32_t)c[0] | ((unsigned long long)(uint32_t)c[1] << 32);
+}
+
+// One column-table entry: the cell on grid axis a of level-L pixel column p
+// (its i when by_j is false, else its j; the other index is 0, whose term is
+// an exact zero), computed with axis_ray_setup's operations; -1 where the
+// column misses the grid.
+__device__ __forceinline__ int axis_table_entry(const GridView &g, const RayGeom &rg, int a, int L,
+                                                int p, bool by_j) {
+  const double pix = rg.pix0 * exp2_neg(L);
+  const double uc = fma((double)(by_j ? 0 : p) + 0.5, pix, -rg.H);
+  const double vc = fma((double)(by_j ? p : 0) + 0.5, pix, -rg.H);
+  const double x = fma(vc, rg.V[a], fma(uc, rg.U[a], rg.C[a]));
+  const double q = __dmul_rn(x, rg.invh[a]);
+  const double o = fma(fma(-q, rg.h[a], x), rg.invh[a], q);
+  return (o >= 0.0 && o < (double)g.nf[a]) ? (int)o : -1;
 }
 
 template <int NBT, int FMT>
@@ -809,7 +876,29 @@ static inline RayGeom make_geom(const GridView &g, const Camera &cam, int n0) {
   }
   rg.H = cam.H;
   rg.pix0 = (2.0 * cam.H) / (double)n0;
+  rg.tab = nullptr;
+  rg.tab_slot = 0;
+  rg.tab_n0 = n0;
+  rg.tab_byj = 0;
   return rg;
 }
+
+// Whether the view's rays run along one grid axis A with u and v along the
+// other two (each with one nonzero component); then *byj gets bit s set when
+// fixed axis (A + 1 + s) % 3 follows v (the pixel's j).
+static inline bool axis_table_view(const RayGeom &rg, int *A, int *byj) {
+  const int moving = (rg.Dhi[0] != 0.f) + (rg.Dhi[1] != 0.f) + (rg.Dhi[2] != 0.f);
+  if (moving != 1) return false;
+  *A = rg.Dhi[0] != 0.f ? 0 : (rg.Dhi[1] != 0.f ? 1 : 2);
+  *byj = 0;
+  for (int s = 0; s < 2; ++s) {
+    const int a = (*A + 1 + s) % 3;
+    const bool u = rg.U[a] != 0.0, v = rg.V[a] != 0.0;
+    if (u == v) return false;
+    if (v) *byj |= 1 << s;
+  }
+  return true;
+}
+
 
 }  // namespace air

@@ -1,16 +1,23 @@
 // air_mlp.cu -- the refinement-depth network: a perceptron 16 -> 64 -> 64 -> 5
 // (ReLU), BF16 weights and activations with FP32 accumulation, trained with
-// softmax cross-entropy and Adam. Not in the paper: it proposes, per base
-// pixel, the depth plain AIR will reach, so the finest rays can be traced in one
-// wave; the paper's criterion still decides the image (air_learned.cu).
+// softmax cross-entropy and Adam. Not in the paper: it proposes, per quadrant
+// of every base pixel, the depth plain AIR will reach, so the finest rays can
+// be traced in one wave; the paper's criterion still decides the image
+// (air_learned.cu).
 //
 // Tensor cores: every layer of the forward pass and both data-gradient
 // products of the backward pass are mma.sync m16n8k16 (BF16 in, FP32 out). A
 // warp owns 32 samples (two 16-row tiles); the FP32 accumulator fragments of
 // two adjacent 8-column tiles are exactly the BF16 A-operand fragment of the
-// next 16-wide K slice, so layers chain in registers. Weight gradients are
-// sums over the block's 128 samples in FP32 from shared memory, reduced over
-// blocks in a fixed order (deterministic).
+// next 16-wide K slice, so layers chain in registers. The weight gradients
+// dW = act^T d over the block's 128 samples are mma.sync products as well:
+// the activations are staged in BF16 (as the forward used them) and read
+// transposed by ldmatrix.trans; each d is staged as two BF16 parts, hi =
+// bf16(d) and lo = bf16(d - hi), and both products are accumulated, so d
+// keeps about 16 significant bits (error <= 2^-16 |d| per term, against the
+// FP32 sums of the plain form's 2^-24). Bias gradients are column sums of
+// hi + lo. Per-block sums are reduced over blocks in a fixed order
+// (deterministic).
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -54,6 +61,30 @@ __device__ __forceinline__ void mma16816(float d[4], const uint32_t a[4], uint32
       "{%0,%1,%2,%3};\n"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// ldmatrix: four (two) 8 x 8 BF16 blocks, transposed; lane l gives the
+// address of row l & 7 of block l >> 3 (16-byte aligned) and receives
+// elements (2 (l & 3), l >> 2) and (2 (l & 3) + 1, l >> 2) of each block.
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t r[4], const void *p) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(s));
+}
+__device__ __forceinline__ void ldsm_x2_trans(uint32_t r[2], const void *p) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(s));
+}
+
+// Two values of d as BF16 parts: hi = bf16(v), lo = bf16(v - hi), two per
+// word (v0 in the low half).
+__device__ __forceinline__ void stage_hi_lo(uint32_t *h, uint32_t *l, int w, float v0, float v1) {
+  const uint32_t hw = pack_bf16(v0, v1);
+  h[w] = hw;
+  l[w] = pack_bf16(v0 - bf16_lo(hw), v1 - bf16_hi(hw));
 }
 
 __global__ void k_pack_weights(const float *__restrict__ th, uint32_t *__restrict__ w) {
@@ -104,10 +135,12 @@ __global__ void __launch_bounds__(kTile) k_mlp(MlpArgs a) {
   uint32_t *xs = sm + kWords;                 // [128][8]
   uint32_t *h1s = xs + kTile * (kIn / 2);     // [128][32]
   uint32_t *h2s = h1s + kTile * (kH / 2);     // [128][32]
-  float *d1s = reinterpret_cast<float *>(h2s + kTile * (kH / 2));  // [128][64]
-  float *d2s = d1s + kTile * kH;              // [128][64]
-  float *d3s = d2s + kTile * kH;              // [128][8]
-  float *lsum = d3s + kTile * kOutP;          // [4] per-warp loss
+  // back-propagated errors, two BF16 parts each (hi, lo), two per word along
+  // the output unit: d1 and d2 [128][64], d3 [128][8]
+  uint32_t *d1h = h2s + kTile * (kH / 2), *d1l = d1h + kTile * (kH / 2);
+  uint32_t *d2h = d1l + kTile * (kH / 2), *d2l = d2h + kTile * (kH / 2);
+  uint32_t *d3h = d2l + kTile * (kH / 2), *d3l = d3h + kTile * (kOutP / 2);
+  float *lsum = reinterpret_cast<float *>(d3l + kTile * (kOutP / 2));  // [4] per-warp loss
   __syncthreads();
   const uint32_t *W1T = sw + kW1T, *W2T = sw + kW2T, *W3T = sw + kW3T, *W3P = sw + kW3P, *W2R = sw + kW2R;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
@@ -218,10 +251,8 @@ __global__ void __launch_bounds__(kTile) k_mlp(MlpArgs a) {
       if (vr && yr == 2 * t) wloss -= logf(p0);
       if (vr && yr == 2 * t + 1) wloss -= logf(p1);
     }
-    d3s[la * kOutP + 2 * t] = d3[0];
-    d3s[la * kOutP + 2 * t + 1] = d3[1];
-    d3s[lb * kOutP + 2 * t] = d3[2];
-    d3s[lb * kOutP + 2 * t + 1] = d3[3];
+    stage_hi_lo(d3h, d3l, la * (kOutP / 2) + t, d3[0], d3[1]);
+    stage_hi_lo(d3h, d3l, lb * (kOutP / 2) + t, d3[2], d3[3]);
     // d2 = (d3 W3^T) * [z2 > 0]
     const uint32_t ad3[4] = {pack_bf16(d3[0], d3[1]), pack_bf16(d3[2], d3[3]), 0u, 0u};
 #pragma unroll
@@ -233,10 +264,8 @@ __global__ void __launch_bounds__(kTile) k_mlp(MlpArgs a) {
       if (bf16_hi(hg) == 0.f) acc[nt][1] = 0.f;
       if (bf16_lo(hg8) == 0.f) acc[nt][2] = 0.f;
       if (bf16_hi(hg8) == 0.f) acc[nt][3] = 0.f;
-      d2s[la * kH + nt * 8 + 2 * t] = acc[nt][0];
-      d2s[la * kH + nt * 8 + 2 * t + 1] = acc[nt][1];
-      d2s[lb * kH + nt * 8 + 2 * t] = acc[nt][2];
-      d2s[lb * kH + nt * 8 + 2 * t + 1] = acc[nt][3];
+      stage_hi_lo(d2h, d2l, la * (kH / 2) + nt * 4 + t, acc[nt][0], acc[nt][1]);
+      stage_hi_lo(d2h, d2l, lb * (kH / 2) + nt * 4 + t, acc[nt][2], acc[nt][3]);
     }
     uint32_t ad2[4][4];
 #pragma unroll
@@ -258,10 +287,8 @@ __global__ void __launch_bounds__(kTile) k_mlp(MlpArgs a) {
       if (bf16_hi(hg) == 0.f) acc[nt][1] = 0.f;
       if (bf16_lo(hg8) == 0.f) acc[nt][2] = 0.f;
       if (bf16_hi(hg8) == 0.f) acc[nt][3] = 0.f;
-      d1s[la * kH + nt * 8 + 2 * t] = acc[nt][0];
-      d1s[la * kH + nt * 8 + 2 * t + 1] = acc[nt][1];
-      d1s[lb * kH + nt * 8 + 2 * t] = acc[nt][2];
-      d1s[lb * kH + nt * 8 + 2 * t + 1] = acc[nt][3];
+      stage_hi_lo(d1h, d1l, la * (kH / 2) + nt * 4 + t, acc[nt][0], acc[nt][1]);
+      stage_hi_lo(d1h, d1l, lb * (kH / 2) + nt * 4 + t, acc[nt][2], acc[nt][3]);
     }
   }
   if (!TRAIN) return;
@@ -269,33 +296,65 @@ __global__ void __launch_bounds__(kTile) k_mlp(MlpArgs a) {
   for (int off = 16; off > 0; off >>= 1) wloss += __shfl_xor_sync(0xffffffffu, wloss, off);
   if (lane == 0) lsum[warp] = wloss;
   __syncthreads();
-  // weight gradients: sums over the tile's 128 samples (fixed order)
-  const uint16_t *xh = reinterpret_cast<const uint16_t *>(xs);
-  const uint16_t *h1h = reinterpret_cast<const uint16_t *>(h1s);
-  const uint16_t *h2h = reinterpret_cast<const uint16_t *>(h2s);
+  // weight gradients: 44 output tiles of 16 x 8 (dW1: 1 x 8, dW2: 4 x 8,
+  // dW3: 4 x 1), a warp taking every fourth; each sums the 128 samples in 8
+  // K steps of 16, hi and lo parts of d in turn (fixed order)
   float *out = a.partial + (int64_t)blockIdx.x * (kNP + 1);
-  for (int j = threadIdx.x; j < kNP; j += blockDim.x) {
-    float s = 0.f;
-    if (j < ob1) {
-      const int k = (j - oW1) / kH, nn = (j - oW1) % kH;
-      for (int r = 0; r < kTile; ++r) s += __uint_as_float((uint32_t)xh[r * kIn + k] << 16) * d1s[r * kH + nn];
-    } else if (j < oW2) {
-      const int nn = j - ob1;
-      for (int r = 0; r < kTile; ++r) s += d1s[r * kH + nn];
-    } else if (j < ob2) {
-      const int k = (j - oW2) / kH, nn = (j - oW2) % kH;
-      for (int r = 0; r < kTile; ++r) s += __uint_as_float((uint32_t)h1h[r * kH + k] << 16) * d2s[r * kH + nn];
-    } else if (j < oW3) {
-      const int nn = j - ob2;
-      for (int r = 0; r < kTile; ++r) s += d2s[r * kH + nn];
-    } else if (j < ob3) {
-      const int k = (j - oW3) / kOut, c = (j - oW3) % kOut;
-      for (int r = 0; r < kTile; ++r) s += __uint_as_float((uint32_t)h2h[r * kH + k] << 16) * d3s[r * kOutP + c];
+  for (int tile = warp; tile < 44; tile += 4) {
+    const uint32_t *act, *dh, *dl;
+    int lda, ldd, m0, n0, ow, ncols;
+    if (tile < 8) {
+      act = xs; lda = kIn; dh = d1h; dl = d1l; ldd = kH; m0 = 0; n0 = tile * 8; ow = oW1; ncols = kH;
+    } else if (tile < 40) {
+      const int u = tile - 8;
+      act = h1s; lda = kH; dh = d2h; dl = d2l; ldd = kH; m0 = (u >> 3) * 16; n0 = (u & 7) * 8;
+      ow = oW2; ncols = kH;
     } else {
-      const int c = j - ob3;
-      for (int r = 0; r < kTile; ++r) s += d3s[r * kOutP + c];
+      act = h2s; lda = kH; dh = d3h; dl = d3l; ldd = kOutP; m0 = (tile - 40) * 16; n0 = 0;
+      ow = oW3; ncols = kOut;
     }
-    out[j] = s;
+    const uint16_t *ah = reinterpret_cast<const uint16_t *>(act);
+    const uint16_t *bh = reinterpret_cast<const uint16_t *>(dh);
+    const uint16_t *bl = reinterpret_cast<const uint16_t *>(dl);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int mi = lane >> 3, j = lane & 7;
+#pragma unroll 2
+    for (int r0 = 0; r0 < kTile; r0 += 16) {
+      // A = act^T: 8 x 8 blocks (samples r0 + 8 (mi >> 1) .., features m0 + 8 (mi & 1) ..)
+      uint32_t fa[4], fb[2], fl[2];
+      ldsm_x4_trans(fa, ah + (r0 + j + ((mi >> 1) << 3)) * lda + m0 + ((mi & 1) << 3));
+      // B = d: 8 x 8 blocks (samples r0 + 8 (mi & 1) .., units n0 ..)
+      const int br = r0 + j + ((mi & 1) << 3);
+      ldsm_x2_trans(fb, bh + br * ldd + n0);
+      ldsm_x2_trans(fl, bl + br * ldd + n0);
+      mma16816(acc, fa, fb[0], fb[1]);
+      mma16816(acc, fa, fl[0], fl[1]);
+    }
+    // D[m][n]: (g, 2t), (g, 2t + 1), (g + 8, 2t), (g + 8, 2t + 1)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int m = m0 + g + ((e >> 1) << 3), n = n0 + 2 * t + (e & 1);
+      if (n < ncols) out[ow + m * ncols + n] = acc[e];
+    }
+  }
+  // bias gradients: column sums of hi + lo over the 128 samples (fixed order)
+  for (int c = threadIdx.x; c < 2 * kH + kOut; c += blockDim.x) {
+    const uint16_t *bh, *bl;
+    int ldd, n, ob;
+    if (c < kH) {
+      bh = reinterpret_cast<const uint16_t *>(d1h); bl = reinterpret_cast<const uint16_t *>(d1l);
+      ldd = kH; n = c; ob = ob1;
+    } else if (c < 2 * kH) {
+      bh = reinterpret_cast<const uint16_t *>(d2h); bl = reinterpret_cast<const uint16_t *>(d2l);
+      ldd = kH; n = c - kH; ob = ob2;
+    } else {
+      bh = reinterpret_cast<const uint16_t *>(d3h); bl = reinterpret_cast<const uint16_t *>(d3l);
+      ldd = kOutP; n = c - 2 * kH; ob = ob3;
+    }
+    float sum = 0.f;
+    for (int r = 0; r < kTile; ++r)
+      sum += __uint_as_float((uint32_t)bh[r * ldd + n] << 16) + __uint_as_float((uint32_t)bl[r * ldd + n] << 16);
+    out[ob + n] = sum;
   }
   if (threadIdx.x == 0) out[kNP] = lsum[0] + lsum[1] + lsum[2] + lsum[3];
 }

@@ -1,8 +1,10 @@
 """GPU refinement-depth network (tensor-core mma.sync BF16 kernels) against the
 FP64 reference oracle/mlp.py. With the reference in its BF16-operand mode the
-only difference left is FP32 versus FP64 accumulation, so logits and
-gradients agree to ~1e-5 of their scale; against the plain FP64 network the
-BF16 bound (~3e-2 of the gradient norm) applies."""
+differences left are FP32 versus FP64 accumulation and, in the weight
+gradients, the back-propagated errors carried as two BF16 parts (about 16
+significant bits, <= 2^-16 relative per term), so logits agree to ~1e-5 and
+gradients well inside 2e-3 of their scale; against the plain FP64 network
+the BF16 bound (~3e-2 of the gradient norm) applies."""
 import numpy as np
 import pytest
 
