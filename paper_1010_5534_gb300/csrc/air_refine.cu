@@ -77,32 +77,6 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(const int32_t *bcount, int
   if (threadIdx.x == 1023) *total = part[1023];
 }
 
-// Round-by-round block scan; calls emit(k, rank) for every selected item.
-template <class Pred, class Emit>
-__device__ __forceinline__ void block_scan_emit(Pred pred, Emit &emit, int64_t n, int64_t boff) {
-  __shared__ int32_t wsum[kScanBlock / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t start = (int64_t)blockIdx.x * kScanItems;
-  int64_t run = boff;
-  for (int rr = 0; rr < kScanRounds; ++rr) {
-    const int64_t k = start + (int64_t)rr * kScanBlock + threadIdx.x;
-    const bool p = k < n && pred(k);
-    const uint32_t bal = __ballot_sync(0xffffffffu, p);
-    if (lane == 0) wsum[warp] = __popc(bal);
-    __syncthreads();
-    int32_t before = 0, tot = 0;
-#pragma unroll
-    for (int w = 0; w < kScanBlock / 32; ++w) {
-      const int32_t v = wsum[w];
-      before += w < warp ? v : 0;
-      tot += v;
-    }
-    if (p) emit(k, run + before + __popc(bal & ((1u << lane) - 1u)));
-    run += tot;
-    __syncthreads();
-  }
-}
-
 // ---- open-leaf list -----------------------------------------------------------
 // The leaves below the top level, in ascending node order: the only nodes a
 // sweep can flag. Steps iii and iv run over this list instead of every node;
@@ -481,25 +455,62 @@ __global__ void __launch_bounds__(kScanBlock) k_emit3d(TreeView t, int32_t *open
 }
 
 // Step vi: copy the selected nodes (leaves, or all) to the output arrays.
-struct EmitOut {
-  TreeView t;
-  OutView o;
-  __device__ void operator()(int64_t k, int64_t r) {
-    if (o.level) o.level[r] = t.lvl[k];
-    if (o.i) o.i[r] = t.pi[k];
-    if (o.j) o.j[r] = t.pj[k];
-    if (o.is_leaf) o.is_leaf[r] = t.child[k] < 0;
-    if (o.N) o.N[r] = t.N[k];
-    if (o.p) o.p[r] = t.p[k];
-    if (o.I)
-      for (int b = 0; b < o.n_bands; ++b) o.I[(int64_t)b * o.stride + r] = t.I[(int64_t)b * t.cap + k];
-  }
-};
 
+// The fields of every round's node are loaded before the ranks are formed,
+// so their latency overlaps the block's ballots and barriers.
 __global__ void __launch_bounds__(kScanBlock) k_emit_out(TreeView t, OutView o, int all, int64_t n,
                                                          const int64_t *boff) {
-  EmitOut e{t, o};
-  block_scan_emit(PredLeaf{t.child, all}, e, n, boff[blockIdx.x]);
+  __shared__ int32_t wsum[kScanBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t start = (int64_t)blockIdx.x * kScanItems;
+  bool sel[kScanRounds];
+  int lv[kScanRounds], pi[kScanRounds], pj[kScanRounds], cl[kScanRounds];
+  float N[kScanRounds], P[kScanRounds], I0[kScanRounds];
+#pragma unroll
+  for (int rr = 0; rr < kScanRounds; ++rr) {
+    const int64_t k = start + (int64_t)rr * kScanBlock + threadIdx.x;
+    sel[rr] = false;
+    if (k < n) {
+      cl[rr] = t.child[k];
+      sel[rr] = all || cl[rr] < 0;
+      lv[rr] = t.lvl[k];
+      pi[rr] = t.pi[k];
+      pj[rr] = t.pj[k];
+      N[rr] = t.N[k];
+      P[rr] = t.p[k];
+      I0[rr] = o.I ? t.I[k] : 0.f;  // no tree intensities are read without o.I
+    }
+  }
+  int64_t run = boff[blockIdx.x];
+#pragma unroll
+  for (int rr = 0; rr < kScanRounds; ++rr) {
+    const int64_t k = start + (int64_t)rr * kScanBlock + threadIdx.x;
+    const uint32_t bal = __ballot_sync(0xffffffffu, sel[rr]);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    int32_t before = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kScanBlock / 32; ++w) {
+      const int32_t v = wsum[w];
+      before += w < warp ? v : 0;
+      tot += v;
+    }
+    if (sel[rr]) {
+      const int64_t r = run + before + __popc(bal & ((1u << lane) - 1u));
+      if (o.level) o.level[r] = lv[rr];
+      if (o.i) o.i[r] = pi[rr];
+      if (o.j) o.j[r] = pj[rr];
+      if (o.is_leaf) o.is_leaf[r] = cl[rr] < 0;
+      if (o.N) o.N[r] = N[rr];
+      if (o.p) o.p[r] = P[rr];
+      if (o.I) {
+        o.I[r] = I0[rr];
+        for (int b = 1; b < o.n_bands; ++b) o.I[(int64_t)b * o.stride + r] = t.I[(int64_t)b * t.cap + k];
+      }
+    }
+    run += tot;
+    __syncthreads();
+  }
 }
 
 // Base image, row-major: node j*n0 + i.
@@ -541,11 +552,29 @@ __global__ void __launch_bounds__(256) k_flux_partial(FluxArgs a) {
   }
   if (threadIdx.x == 0) outp[0] = (double)shs[0];
   for (int b = 0; b < a.n_bands; ++b) {
-    double s = 0.0;
+    // a thread's leaves summed as an unevaluated pair of FP32 numbers
+    // (Knuth's two-sum: hi + lo carries the sum to ~2^-44 relative) of
+    // I 4^-L, an exact scaling while the product stays a normal number; the
+    // rare smaller terms go to an FP64 sum. FP64 work per thread, not per
+    // leaf (FP64 issues at 1/64 of the FP32 rate here).
+    float hi = 0.f, lo = 0.f;
+    double tiny = 0.0;
     for (int64_t k = start + threadIdx.x; k < end; k += blockDim.x) {
       const bool leaf = a.child ? a.child[k] < 0 : true;
-      if (leaf) s = fma((double)a.I[(int64_t)b * a.stride + k], area[a.lvl ? a.lvl[k] : 0], s);
+      if (!leaf) continue;
+      const int L = a.lvl ? a.lvl[k] : 0;
+      const float I = a.I[(int64_t)b * a.stride + k];
+      const float x = __fmul_rn(I, __int_as_float((127 - 2 * L) << 23));
+      if (fabsf(x) >= 0x1p-126f || x == 0.f) {
+        const float t = __fadd_rn(hi, x);
+        const float bv = __fsub_rn(t, hi);
+        lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bv)), __fsub_rn(x, bv)));
+        hi = t;
+      } else {
+        tiny = fma((double)I, area[L], tiny);
+      }
     }
+    double s = fma(((double)hi + (double)lo), a.area0, tiny);
     sh[threadIdx.x] = s;
     __syncthreads();
     for (int off = 128; off > 0; off >>= 1) {

@@ -215,10 +215,57 @@ __device__ __forceinline__ uint32_t xi_flag(const TreeView &t, NodeLookup look, 
 // Step iii, balance: a flagged leaf at level L forces every leaf at a level
 // < L that covers one of its 8 same-level neighbours, and so on down the
 // levels. Each newly set flag is expanded by the thread that set it.
+//
+// With level maps (single-view trees) a neighbour needs one load: the maps
+// of levels below the top level are complete, so a level-L entry that exists
+// is a level-L node (nothing to force) and an entry of -1 means no level-L
+// node covers that pixel, so the deepest node covering it is a leaf at a
+// level below L: it is forced without reading it. The eight entries are
+// loaded together; only the missing ones are looked up one level up.
+__device__ __forceinline__ void balance_from_maps(const TreeView &t, const int32_t *__restrict__ lmap,
+                                                  int k0, uint32_t *__restrict__ flag,
+                                                  uint32_t *__restrict__ err,
+                                                  int (&stack)[kBalanceStack]) {
+  int sp = 0;
+  int q = k0;
+  for (;;) {
+    const int L = t.lvl[q], i = t.pi[q], j = t.pj[q];
+    if (L >= 1) {  // level-0 neighbours always exist
+      const int nl = t.n0 << L;
+      const int32_t *mL = lmap + level_map_offset(t.n0, L);
+      int e[8];
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        const int dd = d < 4 ? d : d + 1;  // skip the centre of the 3x3 stencil
+        const int ii = i + dd % 3 - 1, jj = j + dd / 3 - 1;
+        const bool in = ii >= 0 && jj >= 0 && ii < nl && jj < nl;
+        e[d] = in ? __ldg(mL + (int64_t)jj * nl + ii) : 0;
+      }
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        if (e[d] >= 0) continue;
+        const int dd = d < 4 ? d : d + 1;
+        const int ii = i + dd % 3 - 1, jj = j + dd / 3 - 1;
+        const int m = map_deepest(t, lmap, L - 1, ii >> 1, jj >> 1);
+        if (atomicExch(flag + m, 1u) == 0u) {
+          if (sp < kBalanceStack) stack[sp++] = m;
+          else atomicOr(err, 1u);
+        }
+      }
+    }
+    if (sp == 0) break;
+    q = stack[--sp];
+  }
+}
+
 __device__ __forceinline__ void balance_from(const TreeView &t, NodeLookup look, int k0,
                                              uint32_t *__restrict__ flag,
                                              uint32_t *__restrict__ err) {
   int stack[kBalanceStack];
+  if (look.lmap) {
+    balance_from_maps(t, look.lmap, k0, flag, err, stack);
+    return;
+  }
   int sp = 0;
   stack[sp++] = k0;
   while (sp > 0) {
