@@ -404,6 +404,13 @@ __global__ void __launch_bounds__(kScanBlock) k_emit3d(TreeView t, int32_t *open
     for (int rr = 0; rr < kScanRounds; ++rr) {
       int k;
       const ListSel q = list_sel(t, open, m, flag, t.Lm, start + (int64_t)rr * kScanBlock + threadIdx.x, k);
+      // a flagged node's fields, loaded before the ranks are formed
+      int Lc = 0, pi = 0, pj = 0;
+      if (q.f) {
+        Lc = t.lvl[k] + 1;
+        pi = t.pi[k];
+        pj = t.pj[k];
+      }
       const uint32_t b0 = __ballot_sync(0xffffffffu, q.f);
       const uint32_t b1 = __ballot_sync(0xffffffffu, q.keep);
       const uint32_t b2 = __ballot_sync(0xffffffffu, q.co);
@@ -426,7 +433,7 @@ __global__ void __launch_bounds__(kScanBlock) k_emit3d(TreeView t, int32_t *open
       }
       if (q.f) {
         const int64_t c0 = n_old + 4 * (run0 + p0 + __popc(b0 & below));
-        const int L = t.lvl[k] + 1, i = t.pi[k], j = t.pj[k];
+        const int L = Lc, i = pi, j = pj;
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch) {
           t.lvl[c0 + ch] = (int8_t)L;
