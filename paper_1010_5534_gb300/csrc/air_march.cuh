@@ -176,10 +176,6 @@ __device__ __forceinline__ void prefetch_cell(const void *__restrict__ cells, Id
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
-// (1 - e^-x) / x for 0 <= x < 2^-12 to first order: 1 - x / 2 (remainder
-// < x^2 / 6 < 1e-8).
-__device__ __forceinline__ float one_minus_exp_over_x_first(float x) { return fmaf(-0.5f, x, 1.0f); }
-
 // (1 - e^-x) / x for 0 <= x < 1/64 from its Taylor series truncated after
 // x^3 (remainder < x^4 / 5! < 5e-10).
 __device__ __forceinline__ float one_minus_exp_over_x_short(float x) {
@@ -197,26 +193,31 @@ __device__ __forceinline__ float one_minus_exp_over_x_short(float x) {
 // sums with Kahan compensation; the error of a plain sum of U = 16 positive
 // terms is at most 15 u of the group's sum (u = 2^-24), so the column's sums
 // stay within about 16 u of exact. T_b at each cell is 2^(nk_b N_k) with N_k
-// the running column density plus the group's partial sum (one rounding).
-// FORM 3: every dtau of the group below 2^-12 (the first-order series; used
-// for one-band grids with per-cell Lambda, the format whose instantiations
-// are few enough to afford another form);
+// the running column density plus the group's partial sum, its exponent
+// formed as fma(nk_b, partial, nk_b N_start).
+// FORM 3: every dtau of the group below 2^-12: (1 - e^-x) / x taken to first
+// order, 1 - x / 2 (remainder < x^2 / 6 < 1e-8), as T + (-kappa_b / 2 T)(rho
+// ds); used for one-band grids with per-cell Lambda, the format whose
+// instantiations are few enough to afford another form;
 // FORM 2: below 1/64 (the short series); FORM 1: below 1/4 (the full series);
 // FORM 0: the form is selected per cell and band.
 template <int NBT, int FMT, int FORM, int U>
 __device__ __forceinline__ void column_group(RTState<NBT> &r, const float (&rh)[U],
                                              const uint32_t (&xv)[U], float ds, const BandCtx &bc,
                                              const BandRegs<NBT> &br) {
-  float pN = 0.f, pI[NBT];
-#pragma unroll
-  for (int b = 0; b < NBT; ++b) pI[b] = 0.f;
+  float pN = 0.f, pI[NBT], nN0[NBT], hk[NBT];
   const float N0 = r.N;
+#pragma unroll
+  for (int b = 0; b < NBT; ++b) {
+    pI[b] = 0.f;
+    nN0[b] = __fmul_rn(br.nk[b], N0);  // log2 T_b at the group's start
+    hk[b] = -0.5f * br.kap[b];         // exact: a power-of-two scaling
+  }
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const float rho = rh[u];
     const float rds = __fmul_rn(rho, ds);
     pN = __fadd_rn(pN, rds);
-    const float Nk = __fadd_rn(N0, pN);
     int k = 0;
     float w = 0.f, lam1 = 1.f;
     if (FMT == kCellXq) {
@@ -233,17 +234,19 @@ __device__ __forceinline__ void column_group(RTState<NBT> &r, const float (&rh)[
           const float *t = bc.tab + b * bc.tstride + k;
           lam = fmaf(w, t[1] - t[0], t[0]);
         }
-        const float dtau = __fmul_rn(br.kap[b], rds);
-        const float Tn = ex2_approx(__fmul_rn(br.nk[b], Nk));
+        const float Tn = ex2_approx(fmaf(br.nk[b], pN, nN0[b]));
         const float rl = __fmul_rn(rho, lam);
         float P, Q;
         if (FORM == 3) {
+          // T (1 - dtau / 2) with dtau = kappa_b (rho ds)
           P = __fmul_rn(rl, rds);
-          Q = __fmul_rn(r.T[b], one_minus_exp_over_x_first(dtau));
+          Q = fmaf(__fmul_rn(hk[b], r.T[b]), rds, r.T[b]);
         } else if (FORM == 2) {
+          const float dtau = __fmul_rn(br.kap[b], rds);
           P = __fmul_rn(rl, rds);
           Q = __fmul_rn(r.T[b], one_minus_exp_over_x_short(dtau));
         } else {
+          const float dtau = __fmul_rn(br.kap[b], rds);
           const float Ps = __fmul_rn(rl, rds);
           const float Qs = __fmul_rn(r.T[b], one_minus_exp_over_x(dtau));
           if (FORM == 1) {

@@ -5,6 +5,8 @@ Tolerance: every pixel value (column density N, intensity I_b) within
 maximum for pixels whose value comes from a sliver of a cell (a grazing
 chord, where FP32 ray geometry dominates). Integer results (the refinement
 tree, pixel layout, step counts on axis views) are compared exactly."""
+import math
+
 import numpy as np
 import pytest
 
@@ -117,6 +119,28 @@ def test_fixed_amr_multiband(cone4, fp64_level):
             close(I[b], f["inten"][:, b], f"I[{b}] {v.dir}")
         pf = f["inten"].sum(axis=1)
         close(np_(r["p"]), pf, "p")
+
+
+def test_axis_rays_with_and_without_column_tables(cone4):
+    """Rays along a grid axis take their two fixed cells from a per-column
+    table when the image plane's u and v are grid axes too, and from the FP64
+    set-up otherwise (+z with the image plane turned 30 degrees about it).
+    Both agree with the oracle, step counts exactly; and the table path gives
+    the same bits as the batched kernel, which always takes the FP64 set-up."""
+    sc, g, o = cone4
+    c, s_ = math.cos(math.radians(30.0)), math.sin(math.radians(30.0))
+    turned = scenes.View(dir=(0.0, 0.0, 1.0), up=(s_, c, 0.0))
+    for v in (scenes.axis_view("+z"), turned):
+        r, f = fixed_pair(sc, g, o, v, 77)
+        close(np_(r["coldens"]), f["col"], f"N {v.up}")
+        close(np_(r["intensity"])[0], f["inten"][:, 0], f"I {v.up}")
+        assert r["n_steps"] == int(f["steps"].sum())
+        _hybrid_check(g, o, v, 16, 3, 0.4)
+    v = scenes.axis_view("+z")
+    a = g.render_adaptive(v, 16, 3, 0.4)
+    b = g.render_batch([v], 16, 3, 0.4)[0]
+    for k in ("level", "i", "j", "coldens", "intensity"):
+        assert (np_(a[k]) == np_(b[k])).all(), k
 
 
 def test_fixed_image_missing_the_box(wind):
