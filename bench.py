@@ -735,6 +735,52 @@ def large_view_record(air, torch, st, reps=2):
     return rec
 
 
+def batch_record(air, torch, st):
+    """The batched configuration in brief: the cone grid with 16 bands
+    (0.5-10 keV) at 64 random views, one persistent launch (8 bands per
+    thread), against fixed 4096^2 images of two of the views (extrapolated to
+    64) with the band-summed flux error on those two, and the batched march's
+    FP32-issue fraction. Scene generation, upload and one warm-up render are
+    outside the timed render."""
+    W = WORKLOAD
+    t0 = time.perf_counter()
+    sc = scenes.cone_shock_amr(W["seed"], n_base=W["n_base"], brick=W["brick"], levels=W["levels"],
+                               n_bands=16, e_lo=0.5, e_hi=10.0)
+    g = air.Grid(sc)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    vs = scenes.random_views(3, 64)
+    n0, Lm, xc = W["base_res"], W["max_level"], W["xi_crit"]
+    g.render_batch(vs, n0, Lm, xc, bands_per_thread=8, fields=("band_flux",))
+    g.profile(True)
+    ms, b = _timed(lambda: g.render_batch(vs, n0, Lm, xc, bands_per_thread=8, fields=("band_flux",)), st)
+    prof = g.profile_read()
+    g.profile(False)
+    steps = sum(r["n_steps"] for r in b)
+    g.render_fixed(vs[0], 512, fields=("band_flux",))
+    fx = [_timed(lambda: g.render_fixed(v, W["fixed_res"], fields=("band_flux",)), st) for v in vs[:2]]
+    fixed_view_ms = float(np.mean([x[0] for x in fx]))
+    ferr = [abs(float(b[k]["band_flux"].double().sum()) - float(fx[k][1]["band_flux"].double().sum())) /
+            abs(float(fx[k][1]["band_flux"].double().sum())) for k in range(2)]
+    band_steps_s = 16 * steps / (prof["batch"][0] * 1e-3)
+    peak_ops = 152 * 128 * 2.07e9
+    rec = dict(workload="cone grid, 64 random views x 16 bands (0.5-10 keV), base 256^2, max level 4, "
+                        "xi_crit 0.5, one persistent launch, 8 bands per thread",
+               setup_s=setup_s, batched_ms=ms, rays=int(sum(r["n_rays"] for r in b)), steps=int(steps),
+               band_steps_per_s=16 * steps / ms * 1e3, kernel_ms=prof["batch"][0],
+               fixed_per_view_ms=fixed_view_ms, fixed_64_views_ms_extrapolated=fixed_view_ms * len(vs),
+               batched_speedup_vs_fixed=fixed_view_ms * len(vs) / ms,
+               flux_rel_err_vs_fixed_views_0_1=ferr,
+               roofline={"bound": "alu", "achieved": band_steps_s * FP32_OPS_PER_BAND_STEP / 1e12,
+                         "peak": peak_ops / 1e12, "unit": "T FP32 op/s",
+                         "frac": band_steps_s * FP32_OPS_PER_BAND_STEP / peak_ops,
+                         "ops_per_band_step": FP32_OPS_PER_BAND_STEP, "kernel": "k_air_batch"})
+    g.close()
+    del sc, g
+    torch.cuda.empty_cache()
+    return rec
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -754,6 +800,8 @@ def main():
                     help="samples of the --workload mlp run")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the one-view record of the large configuration")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the record of the 64-view batched configuration")
     ap.add_argument("--clocks-file", default=None,
                     help="keep the nvidia-smi clock samples here ({rank} is replaced by the rank); "
                          "default: a temporary file")
@@ -984,6 +1032,9 @@ def main():
         g.close()
         torch.cuda.empty_cache()
         large = large_view_record(air, torch, st)
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batch:
+        batched = batch_record(air, torch, st)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -1004,6 +1055,7 @@ def main():
             flux_rel_err_vs_fixed=flux_err,
             learned_proposal=learned,
             large_view=large,
+            batched_64_views=batched,
             phase_ms_per_image={k: v[0] / args.steps for k, v in prof.items()},
             profiled_pass_ms_per_image=sum(prof_step_ms) / args.steps,
             phase_source="second timed pass of the same images with the library's CUDA-event "
