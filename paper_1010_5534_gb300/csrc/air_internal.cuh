@@ -88,6 +88,35 @@ __host__ __device__ __forceinline__ int64_t prop_rays(const int8_t *d4) {
   for (int q = 0; q < 4; ++q) s += d4[q] > 1 ? prop_subtree(d4[q] - 1) : 0;
   return s;
 }
+// Pixel (L, i, j) of ray r (0 <= r < prop_rays(d4)) of base pixel (bi, bj)'s
+// proposal: the four level-1 pixels first, then each quadrant's subtree level
+// by level, row-major within a level. prop_index inverts it.
+__host__ __device__ __forceinline__ void prop_ray(const int8_t *d4, int64_t r, int bi, int bj,
+                                                  int &L, int &i, int &j) {
+  if (r < 4) {
+    L = 1;
+    i = 2 * bi + (int)(r & 1);
+    j = 2 * bj + (int)(r >> 1);
+    return;
+  }
+  int64_t rr = r - 4;
+  int q = 0;
+  while (q < 3) {
+    const int64_t sz = d4[q] > 1 ? prop_subtree(d4[q] - 1) : 0;
+    if (rr < sz) break;
+    rr -= sz;
+    ++q;
+  }
+  const int e = d4[q] - 1;  // the quadrant's subtree depth (>= 1 here)
+  int Lr = 1;
+  while (Lr < e && rr >= prop_level_offset(Lr + 1)) ++Lr;
+  const int64_t loc = rr - prop_level_offset(Lr);
+  const int w = 1 << Lr;
+  L = Lr + 1;
+  i = ((2 * bi + (q & 1)) << Lr) + (int)(loc % w);
+  j = ((2 * bj + (q >> 1)) << Lr) + (int)(loc / w);
+}
+
 // Ray of pixel (L, i, j), L >= 1, in the proposal of the base pixel that
 // holds it (quadrant depths d4, first ray off), or -1 if it was not traced.
 __host__ __device__ __forceinline__ int64_t prop_index(const int8_t *d4, int64_t off, int L, int i,

@@ -234,29 +234,11 @@ __global__ void __launch_bounds__(256) k_prop_fill(const int8_t *depth, int64_t 
   const int64_t nn0 = (int64_t)n0 * n0;
   const int64_t r0 = k % nn0;
   const int bi = (int)(r0 % n0), bj = (int)(r0 / n0);
-  int64_t qsz[4];
-  for (int q = 0; q < 4; ++q) qsz[q] = d4[q] > 1 ? prop_subtree(d4[q] - 1) : 0;
   if (pview)
     for (int64_t r = lane; r < size; r += 32) pview[base + r] = (int16_t)(k / nn0);
   for (int64_t r = lane; r < size; r += 32) {
     int L, i, j;
-    if (r < 4) {
-      L = 1;
-      i = 2 * bi + (int)(r & 1);
-      j = 2 * bj + (int)(r >> 1);
-    } else {
-      int64_t rr = r - 4;
-      int q = 0;
-      while (q < 3 && rr >= qsz[q]) rr -= qsz[q++];
-      const int e = d4[q] - 1;  // the quadrant's subtree depth (>= 1 here)
-      int Lr = 1;
-      while (Lr < e && rr >= prop_level_offset(Lr + 1)) ++Lr;
-      const int64_t loc = rr - prop_level_offset(Lr);
-      const int w = 1 << Lr;
-      L = Lr + 1;
-      i = ((2 * bi + (q & 1)) << Lr) + (int)(loc % w);
-      j = ((2 * bj + (q >> 1)) << Lr) + (int)(loc / w);
-    }
+    prop_ray(d4, r, bi, bj, L, i, j);
     plvl[base + r] = (int8_t)L;
     ppi[base + r] = i;
     ppj[base + r] = j;
