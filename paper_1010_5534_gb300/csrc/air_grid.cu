@@ -26,8 +26,10 @@ namespace air {
 
 // Raw fields -> cell records (see GridView::cell_fmt). The table coordinate
 // of T is x = (log10 T - logT_lo) / dlogT * (n_tbins - 1), clamped; for one
-// band, Lambda = (1 - w) tab[k] + w tab[k + 1] with k = floor(x) (at most
-// n_tbins - 2) and w = x - k, in FP64, rounded once to FP32.
+// band the record holds rho Lambda with Lambda = (1 - w) tab[k] + w tab[k + 1],
+// k = floor(x) (at most n_tbins - 2) and w = x - k, formed in FP64 from the
+// stored FP32 rho and rounded once to FP32 (every transfer form uses Lambda
+// only in the product rho Lambda).
 template <typename T>
 __global__ void k_convert_fields(const T *__restrict__ rho_in, const T *__restrict__ t_in,
                                  int64_t n, int fmt, void *__restrict__ out, double logT_lo,
@@ -52,7 +54,8 @@ __global__ void k_convert_fields(const T *__restrict__ rho_in, const T *__restri
       int kk = (int)floor(x);
       if (kk > n_tbins - 2) kk = n_tbins - 2;
       const double w = x - (double)kk;
-      aux = __float_as_uint((float)((1.0 - w) * (double)tab0[kk] + w * (double)tab0[kk + 1]));
+      const double lam = (1.0 - w) * (double)tab0[kk] + w * (double)tab0[kk + 1];
+      aux = __float_as_uint((float)((double)rf * lam));
     } else {
       aux = (uint32_t)rint(x * (double)(1u << kXqFracBits));
     }

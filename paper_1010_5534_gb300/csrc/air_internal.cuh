@@ -23,8 +23,9 @@ struct GridView {
   double lo[3], h[3];   // world origin and finest cell size
   // cell fields, one record per cell (cell_fmt):
   //   kCellRho  : float rho                                 (emission j = rho^2)
-  //   kCellLam  : float2 {rho, Lambda(T)}                   (one band, Lambda
-  //               interpolated once per cell at upload, in FP64)
+  //   kCellLam  : float2 {rho, rho Lambda(T)}               (one band, Lambda
+  //               interpolated and multiplied by rho once per cell at upload,
+  //               in FP64)
   //   kCellXq   : uint2 {rho bits, xq}, xq = round(x 2^24) the fixed-point
   //               table coordinate of T, x = (log10 T - logT_lo) / dlogT in bins
   const void *cells;

@@ -96,7 +96,7 @@ __device__ __forceinline__ void rt_init(RTState<NBT> &r) {
 }
 
 // Transfer step of one cell chord of length ds: density rho, and aux =
-// Lambda (kCellLam, as float bits) or the table coordinate of T (kCellXq).
+// rho Lambda (kCellLam, as float bits) or the table coordinate of T (kCellXq).
 // With dtau = 0 (kappa_b = 0 or rho = 0) the series form gives the optically
 // thin term j ds T exactly, so no separate case is needed.
 // Both forms of the cell term are evaluated and the one for the cell's dtau
@@ -129,7 +129,7 @@ __device__ __forceinline__ void rt_term(RTState<NBT> &r, float rho, uint32_t aux
       }
       const float dtau = br.kap[b] * rds;
       const float Tn = ex2_approx(br.nk[b] * r.N);
-      const float rl = rho * lam;
+      const float rl = FMT == kCellLam ? lam1 : rho * lam;  // rho Lambda_b
       const float t_small = __fmul_rn(rl * rds, r.T[b] * one_minus_exp_over_x(dtau));
       const float t_large = __fmul_rn(rl * br.ik[b], r.T[b] - Tn);
       const float term = dtau < 0.25f ? t_small : t_large;
@@ -235,7 +235,7 @@ __device__ __forceinline__ void column_group(RTState<NBT> &r, const float (&rh)[
           lam = fmaf(w, t[1] - t[0], t[0]);
         }
         const float Tn = ex2_approx(fmaf(br.nk[b], pN, nN0[b]));
-        const float rl = __fmul_rn(rho, lam);
+        const float rl = FMT == kCellLam ? lam1 : __fmul_rn(rho, lam);  // rho Lambda_b
         float P, Q;
         if (FORM == 3) {
           // T (1 - dtau / 2) with dtau = kappa_b (rho ds)
